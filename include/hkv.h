@@ -1,0 +1,212 @@
+/*
+ * hkv.h - C ABI of a GB300-native (sm_103a) cache-semantic GPU hash table:
+ * the data-parallel hot path of HierarchicalKV (arxiv 2603.17168).
+ *
+ * A table is a power-of-two number B of buckets of S = 128 slots. Each
+ * bucket keeps, in HBM, a 128-byte line of 8-bit digests (one per slot),
+ * 128 uint64 keys and 128 uint64 scores; values (dim fp32 each) live in a
+ * separate arena addressed by (bucket, slot), spilling past an HBM budget
+ * into pinned host memory (Sec. 3.2, Fig. 4; Sec. 3.6; Sec. 4.2).
+ *
+ * Conventions for every call below:
+ *  - Array arguments are DEVICE pointers (or pinned, mapped host pointers
+ *    that the device can read) owned by the caller; the library never frees
+ *    or retains them after the call's work completes on `stream`.
+ *    Value arrays are row-major [n][dim] fp32.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *    default stream) unless stated otherwise. Outputs are valid once the
+ *    stream reaches the call's completion point.
+ *  - Each call takes its role of the triple-group protocol (Sec. 3.5,
+ *    Table 4) on the table: find, contains, size and export are readers;
+ *    assign is an updater; insert_or_assign and erase are inserters.
+ *    Readers run concurrently with readers, updaters with updaters, and
+ *    every other pair is serialised. The library enforces this across
+ *    streams with CUDA events; calls on one stream are ordered anyway.
+ *  - Errors are returned as hkv_status; no C++ exception crosses the ABI.
+ *    Errors found on the device (a reserved key, a duplicate key in
+ *    deterministic mode, a bounded wait that ran out) are latched in the
+ *    table and returned by the next hkv_sync / hkv_size call; the batch that
+ *    raised them leaves the table unchanged, except HKV_ERR_TIMEOUT.
+ *    hkv_last_error() gives a message for the calling thread's last error.
+ *  - Keys >= 2^63 are reserved (2^64-1 marks an empty slot, 2^64-2 a locked
+ *    one) and may not be inserted.
+ */
+#ifndef HKV_H
+#define HKV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hkv_table_s *hkv_table_t; /* opaque; owned by the library */
+typedef void *hkv_stream_t;              /* a cudaStream_t */
+
+typedef enum {
+  HKV_OK = 0,
+  HKV_ERR_INVALID_ARG = 1,
+  HKV_ERR_RESERVED_KEY = 2,
+  HKV_ERR_DUPLICATE_KEY = 3, /* deterministic mode only */
+  HKV_ERR_OOM = 4,
+  HKV_ERR_CUDA = 5,
+  HKV_ERR_TIMEOUT = 6,
+  HKV_ERR_BUSY = 7
+} hkv_status;
+
+/* Score policies (Sec. 3.3, "Scoring policies"; Table 5). The paper names
+ * them without formulas; this library defines, per insert_or_assign or
+ * assign call (the table step advances by one at the start of each):
+ *   HKV_LRU            score = step, for new and updated keys;
+ *   HKV_LFU            new: m (multiplicity of the key in the batch);
+ *                      hit: old + m, saturating at 2^64-1;
+ *   HKV_EPOCH_LRU      (epoch << 32) | (step & 0xFFFFFFFF);
+ *   HKV_EPOCH_LFU      (epoch << 32) | count, count as LFU saturating at 2^32-1;
+ *   HKV_CUSTOM         the caller's score of the key's last occurrence;
+ *   HKV_CUSTOM_TS_FREQ (epoch << 16) | count, count saturating at 2^16-1,
+ *                      the epoch being the caller's timestamp. */
+typedef enum {
+  HKV_LRU = 0,
+  HKV_LFU = 1,
+  HKV_EPOCH_LRU = 2,
+  HKV_EPOCH_LFU = 3,
+  HKV_CUSTOM = 4,
+  HKV_CUSTOM_TS_FREQ = 5
+} hkv_policy;
+
+/* Per-key result of insert_or_assign (Algorithm 2's outcomes, decided for
+ * the batch as a whole): UPDATED = resident at batch start, value and score
+ * rewritten; INSERTED = new and resident at batch end; REJECTED = new and not
+ * resident at batch end (refused by admission control, or displaced again by
+ * a higher-scoring key of the same batch). Every occurrence of a key in the
+ * batch gets the same status. */
+enum { HKV_ST_UPDATED = 1, HKV_ST_INSERTED = 2, HKV_ST_REJECTED = 3 };
+
+typedef struct {
+  uint64_t capacity;       /* slots wanted; rounded up to 128 * 2^k, >= 128 */
+  uint32_t dim;            /* fp32 elements per value, >= 1 */
+  int32_t policy;          /* hkv_policy */
+  int32_t dual_bucket;     /* 1: two candidate buckets per key (Sec. 3.4) */
+  int32_t deterministic;   /* 1: a batch holding a key twice is refused with
+                              HKV_ERR_DUPLICATE_KEY */
+  uint64_t hbm_value_budget_bytes; /* value bytes kept in HBM; the rest go to
+                                      pinned mapped host memory. 0 = all HBM */
+  uint64_t slice_bytes;    /* value slice size (Sec. 4.2); 0 = 1 GiB. Rounded
+                              to a power-of-two number of buckets */
+} hkv_options;
+
+/* Create a table on the current CUDA device (Sec. 4.2: bucket arrays in HBM,
+ * value slices in HBM up to the budget, then pinned mapped host memory).
+ * Synchronous. All slots start empty; step = epoch = 0. */
+hkv_status hkv_create(const hkv_options *opts, hkv_table_t *out);
+
+/* Free everything the table owns. Synchronous: waits for the table's
+ * outstanding work. */
+hkv_status hkv_destroy(hkv_table_t t);
+
+/* Table geometry. */
+uint64_t hkv_capacity(hkv_table_t t);    /* B * 128 */
+uint64_t hkv_num_buckets(hkv_table_t t); /* B */
+uint32_t hkv_dim(hkv_table_t t);
+uint64_t hkv_hbm_value_slots(hkv_table_t t); /* slots whose values sit in HBM */
+
+/* find (reader; Algorithm 1): for each keys[i], probe its bucket(s) through
+ * the digest line and copy the value of a hit to values_out[i]
+ * ([n][dim]), set found[i] = 1 and scores_out[i] = its score. A miss leaves
+ * values_out[i] and scores_out[i] untouched and sets found[i] = 0.
+ * found and scores_out may be NULL. Scores are never modified. */
+hkv_status hkv_find(hkv_table_t t, uint64_t n, const uint64_t *keys, float *values_out,
+                    uint8_t *found, uint64_t *scores_out, hkv_stream_t stream);
+
+/* contains (reader; Sec. 3.5): found[i] = 1 iff keys[i] is resident. */
+hkv_status hkv_contains(hkv_table_t t, uint64_t n, const uint64_t *keys, uint8_t *found,
+                        hkv_stream_t stream);
+
+/* insert_or_assign (inserter; Algorithms 2 and 3): upsert a batch.
+ * Duplicate keys collapse to one entry: the value of the last occurrence,
+ * and multiplicity m for the LFU-type policies. Keys resident at batch start
+ * are updated in place; the other keys are inserted into a free slot of
+ * their bucket (dual mode: of the less occupied candidate), or, when full,
+ * replace the minimum-(score, key) entry if their (score, key) is larger
+ * (dual mode: the minimum over both candidates), else are rejected.
+ *   values     [n][dim], required.
+ *   scores     [n], required iff policy == HKV_CUSTOM, else ignored (NULL ok).
+ *   status_out [n] HKV_ST_*, may be NULL.
+ *   evicted_keys / evicted_scores / evicted_values ([n], [n], [n][dim]), may
+ *              be NULL: the entries resident at batch start that the batch
+ *              displaced, compacted in unspecified order; their number is
+ *              written to *n_evicted (a DEVICE uint64, may be NULL).
+ * In single-bucket mode the resulting table state, statuses and evicted
+ * set are a function of the state and the batch alone (the largest 128
+ * (score, key) pairs per bucket); in dual mode they depend on the order in
+ * which concurrent keys claim slots. */
+hkv_status hkv_insert_or_assign(hkv_table_t t, uint64_t n, const uint64_t *keys,
+                                const float *values, const uint64_t *scores,
+                                uint8_t *status_out, uint64_t *evicted_keys,
+                                uint64_t *evicted_scores, float *evicted_values,
+                                uint64_t *n_evicted, hkv_stream_t stream);
+
+/* assign (updater; Sec. 3.5): for each resident key, overwrite its value
+ * (last occurrence wins) and score per the policy; HKV_CUSTOM takes scores[]
+ * when given, else keeps the old score. Missing keys are ignored; the bucket
+ * structure never changes. values may be NULL (scores only). */
+hkv_status hkv_assign(hkv_table_t t, uint64_t n, const uint64_t *keys, const float *values,
+                      const uint64_t *scores, hkv_stream_t stream);
+
+/* erase (inserter; Sec. 3.5): remove each resident key; missing keys are
+ * ignored. An emptied slot needs no tombstone (no probe chains). */
+hkv_status hkv_erase(hkv_table_t t, uint64_t n, const uint64_t *keys, hkv_stream_t stream);
+
+/* size (reader): number of resident keys, written to *out (HOST). Synchronises
+ * `stream` and returns any latched device error. */
+hkv_status hkv_size(hkv_table_t t, uint64_t *out, hkv_stream_t stream);
+
+/* export_batch (reader; Sec. 4.1, export_batch_if without a predicate): scan
+ * slots [slot_offset, slot_offset + n_slots) in global slot order (slot =
+ * bucket * 128 + position) and write each occupied one, compacted in
+ * unspecified order, to keys / values / scores / slots (each may be NULL;
+ * room for n_slots entries). The number written goes to *count_out, a DEVICE
+ * uint64. */
+hkv_status hkv_export_batch(hkv_table_t t, uint64_t slot_offset, uint64_t n_slots,
+                            uint64_t *count_out, uint64_t *keys, float *values,
+                            uint64_t *scores, uint64_t *slots, hkv_stream_t stream);
+
+/* Step and epoch used by the score policies (see hkv_policy). Host-side
+ * state: apply to calls issued after this one. */
+hkv_status hkv_set_step(hkv_table_t t, uint64_t step);
+uint64_t hkv_get_step(hkv_table_t t);
+hkv_status hkv_set_epoch(hkv_table_t t, uint64_t epoch);
+
+/* Wait for `stream` and return (and clear) the table's latched device error. */
+hkv_status hkv_sync(hkv_table_t t, hkv_stream_t stream);
+
+/* Outcome counters accumulated on the device by the kernels since the last
+ * reset, copied to out[HKV_COUNTER_COUNT] (HOST); synchronises `stream`. */
+enum {
+  HKV_CNT_FIND_HIT = 0,
+  HKV_CNT_FIND_MISS = 1,
+  HKV_CNT_UNIQUE = 2,   /* distinct keys of upsert/assign batches */
+  HKV_CNT_UPDATED = 3,
+  HKV_CNT_INSERTED = 4, /* claimed a free slot */
+  HKV_CNT_EVICTED = 5,  /* replaced a minimum entry */
+  HKV_CNT_REJECTED = 6, /* refused by admission */
+  HKV_CNT_RETRIES = 7,  /* slot-claim retries after a lost race */
+  HKV_COUNTER_COUNT = 8
+};
+hkv_status hkv_read_counters(hkv_table_t t, uint64_t *out, hkv_stream_t stream);
+hkv_status hkv_reset_counters(hkv_table_t t, hkv_stream_t stream);
+
+/* Launch shape of the probe kernels: threads per key (1, 2, 4, 8, 16 or 32)
+ * for find/contains, and for the update phase of insert_or_assign/assign.
+ * 0 keeps the current choice. The autotuner in the Python package sets
+ * these; defaults follow the value width. */
+hkv_status hkv_set_launch(hkv_table_t t, int find_threads_per_key, int update_threads_per_key);
+
+/* Message of the calling thread's last error ("" if none). */
+const char *hkv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HKV_H */

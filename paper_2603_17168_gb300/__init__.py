@@ -1,1 +1,260 @@
+"""GB300-native cache-semantic GPU hash table (HierarchicalKV hot path,
+arxiv 2603.17168): a thin ctypes binding of the C ABI in include/hkv.h.
 
+Every step of find / insert_or_assign / assign / erase / size / export runs
+in the CUDA library ``libhkv.so`` (built for sm_103a by
+``python -m paper_2603_17168_gb300.build``). This module only marshals
+arguments: it passes the device pointers of torch CUDA tensors and the
+current torch stream. There is no CPU fallback: if the library is missing
+or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libhkv.so")
+
+LRU, LFU, EPOCH_LRU, EPOCH_LFU, CUSTOM, CUSTOM_TS_FREQ = range(6)
+ST_UPDATED, ST_INSERTED, ST_REJECTED = 1, 2, 3
+(CNT_FIND_HIT, CNT_FIND_MISS, CNT_UNIQUE, CNT_UPDATED, CNT_INSERTED, CNT_EVICTED,
+ CNT_REJECTED, CNT_RETRIES) = range(8)
+COUNTER_NAMES = ("find_hit", "find_miss", "unique", "updated", "inserted", "evicted",
+                 "rejected", "retries")
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "RESERVED_KEY", 3: "DUPLICATE_KEY", 4: "OOM",
+                5: "CUDA", 6: "TIMEOUT", 7: "BUSY"}
+SLOTS = 128
+
+# Every C-ABI entry point declared in include/hkv.h with its ctypes signature.
+_u64, _u32, _i32, _vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p
+_P64 = ctypes.POINTER(ctypes.c_uint64)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("capacity", _u64), ("dim", _u32), ("policy", _i32), ("dual_bucket", _i32),
+                ("deterministic", _i32), ("hbm_value_budget_bytes", _u64), ("slice_bytes", _u64)]
+
+
+SIGNATURES = {
+    "hkv_create": (_i32, [ctypes.POINTER(Options), ctypes.POINTER(_vp)]),
+    "hkv_destroy": (_i32, [_vp]),
+    "hkv_capacity": (_u64, [_vp]),
+    "hkv_num_buckets": (_u64, [_vp]),
+    "hkv_dim": (_u32, [_vp]),
+    "hkv_hbm_value_slots": (_u64, [_vp]),
+    "hkv_find": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp, _vp]),
+    "hkv_contains": (_i32, [_vp, _u64, _vp, _vp, _vp]),
+    "hkv_insert_or_assign": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "hkv_assign": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp]),
+    "hkv_erase": (_i32, [_vp, _u64, _vp, _vp]),
+    "hkv_size": (_i32, [_vp, _P64, _vp]),
+    "hkv_export_batch": (_i32, [_vp, _u64, _u64, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "hkv_set_step": (_i32, [_vp, _u64]),
+    "hkv_get_step": (_u64, [_vp]),
+    "hkv_set_epoch": (_i32, [_vp, _u64]),
+    "hkv_sync": (_i32, [_vp, _vp]),
+    "hkv_read_counters": (_i32, [_vp, _P64, _vp]),
+    "hkv_reset_counters": (_i32, [_vp, _vp]),
+    "hkv_set_launch": (_i32, [_vp, _i32, _i32]),
+    "hkv_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+class HKVError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"hkv error {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libhkv.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
+                               "`python -m paper_2603_17168_gb300.build` (nvcc, sm_103a)")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise HKVError(rc, load_library().hkv_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _u64_types():
+    import torch
+    # 64-bit keys and scores: uint64 tensors, or int64 ones holding the same bits
+    return (torch.uint64, torch.int64)
+
+
+def _need(t, dtype, shape, name):
+    if t is None:
+        return
+    ok = t.dtype in dtype if isinstance(dtype, tuple) else t.dtype == dtype
+    if not (t.is_cuda and ok and t.is_contiguous()):
+        raise ValueError(f"{name}: needs a contiguous CUDA tensor of {dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
+
+
+class Table:
+    """One hash table on the current CUDA device (see include/hkv.h)."""
+
+    def __init__(self, capacity: int, dim: int, policy: int = LRU, dual_bucket: bool = False,
+                 deterministic: bool = False, hbm_value_budget_bytes: int = 0,
+                 slice_bytes: int = 0):
+        L = load_library()
+        o = Options(capacity, dim, policy, int(dual_bucket), int(deterministic),
+                    hbm_value_budget_bytes, slice_bytes)
+        h = ctypes.c_void_p()
+        _check(L.hkv_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.dim = dim
+        self.policy = policy
+        self.dual_bucket = bool(dual_bucket)
+        self.capacity = L.hkv_capacity(h)
+        self.num_buckets = L.hkv_num_buckets(h)
+        self.hbm_value_slots = L.hkv_hbm_value_slots(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(load_library().hkv_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # ------------------------------------------------------------- readers
+    def find(self, keys, values_out=None, found=None, scores_out=None, stream=None):
+        import torch
+        n = keys.numel()
+        if values_out is None:
+            values_out = torch.zeros((n, self.dim), dtype=torch.float32, device=keys.device)
+        if found is None:
+            found = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        _need(keys, _u64_types(), (n,), "keys")
+        _need(values_out, torch.float32, (n, self.dim), "values_out")
+        _need(found, torch.uint8, (n,), "found")
+        _need(scores_out, _u64_types(), (n,), "scores_out")
+        _check(load_library().hkv_find(self._h, n, _ptr(keys), _ptr(values_out), _ptr(found),
+                                       _ptr(scores_out), _stream(stream)))
+        return values_out, found, scores_out
+
+    def contains(self, keys, found=None, stream=None):
+        import torch
+        n = keys.numel()
+        if found is None:
+            found = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        _need(keys, _u64_types(), (n,), "keys")
+        _need(found, torch.uint8, (n,), "found")
+        _check(load_library().hkv_contains(self._h, n, _ptr(keys), _ptr(found), _stream(stream)))
+        return found
+
+    def size(self, stream=None) -> int:
+        out = ctypes.c_uint64()
+        _check(load_library().hkv_size(self._h, ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    def export_batch(self, slot_offset=0, n_slots=None, keys=None, values=None, scores=None,
+                     slots=None, count=None, stream=None):
+        """Occupied slots of [slot_offset, slot_offset + n_slots); returns
+        (count tensor, keys, values, scores, slots), entries [:count] valid."""
+        import torch
+        if n_slots is None:
+            n_slots = self.capacity - slot_offset
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if count is None:
+            count = torch.zeros(1, dtype=torch.int64, device=dev)
+        _check(load_library().hkv_export_batch(self._h, slot_offset, n_slots, _ptr(count),
+                                               _ptr(keys), _ptr(values), _ptr(scores),
+                                               _ptr(slots), _stream(stream)))
+        return count, keys, values, scores, slots
+
+    # ------------------------------------------------------ updaters/inserters
+    def insert_or_assign(self, keys, values, scores=None, status_out=None, evicted_keys=None,
+                         evicted_scores=None, evicted_values=None, n_evicted=None, stream=None):
+        import torch
+        n = keys.numel()
+        _need(keys, _u64_types(), (n,), "keys")
+        _need(values, torch.float32, (n, self.dim), "values")
+        _need(scores, _u64_types(), (n,), "scores")
+        _need(status_out, torch.uint8, (n,), "status_out")
+        _need(evicted_keys, _u64_types(), None, "evicted_keys")
+        _need(evicted_scores, _u64_types(), None, "evicted_scores")
+        _need(evicted_values, torch.float32, None, "evicted_values")
+        _need(n_evicted, _u64_types(), (1,), "n_evicted")
+        for t in (evicted_keys, evicted_scores):
+            if t is not None and t.numel() < n:
+                raise ValueError("evicted outputs need room for n entries")
+        if evicted_values is not None and evicted_values.numel() < n * self.dim:
+            raise ValueError("evicted_values needs room for n rows")
+        _check(load_library().hkv_insert_or_assign(
+            self._h, n, _ptr(keys), _ptr(values), _ptr(scores), _ptr(status_out),
+            _ptr(evicted_keys), _ptr(evicted_scores), _ptr(evicted_values), _ptr(n_evicted),
+            _stream(stream)))
+        return status_out
+
+    def assign(self, keys, values=None, scores=None, stream=None):
+        import torch
+        n = keys.numel()
+        _need(keys, _u64_types(), (n,), "keys")
+        _need(values, torch.float32, (n, self.dim), "values")
+        _need(scores, _u64_types(), (n,), "scores")
+        _check(load_library().hkv_assign(self._h, n, _ptr(keys), _ptr(values), _ptr(scores),
+                                         _stream(stream)))
+
+    def erase(self, keys, stream=None):
+        import torch
+        _need(keys, _u64_types(), (keys.numel(),), "keys")
+        _check(load_library().hkv_erase(self._h, keys.numel(), _ptr(keys), _stream(stream)))
+
+    # ---------------------------------------------------------------- state
+    def set_step(self, step: int):
+        _check(load_library().hkv_set_step(self._h, step))
+
+    def get_step(self) -> int:
+        return load_library().hkv_get_step(self._h)
+
+    def set_epoch(self, epoch: int):
+        _check(load_library().hkv_set_epoch(self._h, epoch))
+
+    def sync(self, stream=None):
+        _check(load_library().hkv_sync(self._h, _stream(stream)))
+
+    def read_counters(self, stream=None) -> dict:
+        arr = (ctypes.c_uint64 * 8)()
+        _check(load_library().hkv_read_counters(self._h, arr, _stream(stream)))
+        return dict(zip(COUNTER_NAMES, list(arr)))
+
+    def reset_counters(self, stream=None):
+        _check(load_library().hkv_reset_counters(self._h, _stream(stream)))
+
+    def set_launch(self, find_threads_per_key: int = 0, update_threads_per_key: int = 0):
+        _check(load_library().hkv_set_launch(self._h, find_threads_per_key,
+                                             update_threads_per_key))

@@ -1,0 +1,200 @@
+// Device-side building blocks shared by the hot-path kernels (sm_103a).
+//
+// Table layout in HBM (Sec. 3.2, Fig. 4; Sec. 3.6; Sec. 4.2):
+//   digests [B][128] uint8   one 128-byte line per bucket; 0 = empty slot
+//   keys    [B][128] uint64  2^64-1 = empty, 2^64-2 = locked (slot CAS lock)
+//   scores  [B][128] uint64  the eviction metadata itself (Sec. 3.3)
+//   values  slices of (1 << slice_shift) slots x dim fp32, addressed by the
+//           global slot g = bucket * 128 + position; slice 0.. in HBM, the
+//           rest in pinned, mapped host memory (position-based addressing).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hkv.h"
+
+namespace hkv {
+
+constexpr uint32_t kSlots = 128;
+constexpr uint64_t kEmptyKey = ~0ull;
+constexpr uint64_t kLockedKey = ~0ull - 1;
+constexpr uint64_t kFirstReserved = 1ull << 63;
+constexpr uint64_t kH2Salt = 0x9E3779B97F4A7C15ull;  // second-hash salt (dual mode)
+constexpr int kMaxClaimAttempts = 4096;             // bound on slot-claim retries
+
+struct TableDev {
+  uint8_t* digests;
+  uint64_t* keys;
+  uint64_t* scores;
+  float* values0;            // slice 0 base
+  float* const* slices;      // [n_slices] slice bases (device array)
+  uint64_t bucket_mask;      // B - 1
+  uint32_t dim;
+  uint32_t slice_shift;      // log2(slots per slice)
+  int32_t policy;
+  int32_t dual;
+  uint32_t* err;             // latched device error (first error wins)
+  unsigned long long* counters;  // [HKV_COUNTER_COUNT]
+};
+
+struct ScoreCtx {
+  uint64_t step;
+  uint64_t epoch;
+};
+
+// ------------------------------------------------------------------ hashing
+
+// MurmurHash3 64-bit finaliser (public-domain construction): the table's
+// key hash. b1 = h & (B-1); digest = bits 32..39 of h, 0 folded onto 1.
+__host__ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+__device__ __forceinline__ uint32_t digest_from_hash(uint64_t h) {
+  uint32_t d = (uint32_t)(h >> 32) & 0xFFu;
+  return d == 0 ? 1u : d;
+}
+
+__device__ __forceinline__ uint64_t second_bucket(const TableDev& t, uint64_t key) {
+  return fmix64(key ^ kH2Salt) & t.bucket_mask;
+}
+
+// ------------------------------------------------------------ value arena
+
+__device__ __forceinline__ float* value_ptr(const TableDev& t, uint64_t g) {
+  uint64_t s = g >> t.slice_shift;
+  if (s == 0) return t.values0 + g * t.dim;
+  return t.slices[s] + (g & ((1ull << t.slice_shift) - 1)) * t.dim;
+}
+
+// ------------------------------------------------------------ small helpers
+
+__device__ __forceinline__ void latch_error(uint32_t* err, uint32_t code) {
+  atomicCAS(err, 0u, code);
+}
+
+__device__ __forceinline__ void count_add(const TableDev& t, int which, unsigned long long v) {
+  if (v) atomicAdd(t.counters + which, v);
+}
+
+__device__ __forceinline__ bool sk_less(uint64_t s1, uint64_t k1, uint64_t s2, uint64_t k2) {
+  return s1 < s2 || (s1 == s2 && k1 < k2);
+}
+
+__device__ __forceinline__ uint64_t sat_add(uint64_t a, uint64_t b, uint64_t cap) {
+  uint64_t bb = b < cap ? b : cap;
+  return a > cap - bb ? cap : a + bb;
+}
+
+// Score of a key under the table policy (see hkv_policy in hkv.h).
+__device__ __forceinline__ uint64_t policy_score(int policy, bool hit, uint64_t old, uint64_t m,
+                                                 bool have_caller, uint64_t caller,
+                                                 const ScoreCtx& c) {
+  switch (policy) {
+    case HKV_LRU:
+      return c.step;
+    case HKV_LFU:
+      return hit ? sat_add(old, m, ~0ull) : m;
+    case HKV_EPOCH_LRU:
+      return (c.epoch << 32) | (c.step & 0xFFFFFFFFull);
+    case HKV_EPOCH_LFU: {
+      uint64_t f = hit ? sat_add(old & 0xFFFFFFFFull, m, 0xFFFFFFFFull)
+                       : (m < 0xFFFFFFFFull ? m : 0xFFFFFFFFull);
+      return (c.epoch << 32) | f;
+    }
+    case HKV_CUSTOM:
+      return have_caller ? caller : old;
+    default: {  // HKV_CUSTOM_TS_FREQ
+      uint64_t f = hit ? sat_add(old & 0xFFFFull, m, 0xFFFFull) : (m < 0xFFFFull ? m : 0xFFFFull);
+      return (c.epoch << 16) | f;
+    }
+  }
+}
+
+// Byte mask of slots whose digest byte equals the pattern: SIMD compare of
+// four digests per 32-bit word (Algorithm 1's __vcmpeq4 step).
+__device__ __forceinline__ uint32_t match4(uint32_t word, uint32_t pat4) {
+  return __vcmpeq4(word, pat4);
+}
+
+// Load this lane's share (128/G bytes) of a bucket's digest line.
+// Read-only path unless CG (cache-global, bypass L1) is asked for.
+template <int G, bool CG>
+__device__ __forceinline__ void load_line(const uint8_t* line, int lane_g, uint32_t (&w)[32 / G]) {
+  constexpr int W = 32 / G;  // 32-bit words per lane
+  if constexpr (W >= 4) {
+    const uint4* p = reinterpret_cast<const uint4*>(line) + lane_g * (W / 4);
+#pragma unroll
+    for (int q = 0; q < W / 4; ++q) {
+      uint4 v = CG ? __ldcg(p + q) : __ldg(p + q);
+      w[4 * q + 0] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
+    }
+  } else if constexpr (W == 2) {
+    const uint2* p = reinterpret_cast<const uint2*>(line) + lane_g;
+    uint2 v = CG ? __ldcg(p) : __ldg(p);
+    w[0] = v.x; w[1] = v.y;
+  } else {
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(line) + lane_g;
+    w[0] = CG ? __ldcg(p) : __ldg(p);
+  }
+}
+
+// Probe one bucket for `key` with a group of G lanes (G divides 32). Each
+// lane compares its 128/G digests and confirms matches against the full
+// key. Every lane of the warp must call this (it ends with a warp ballot).
+// Returns the slot (0..127) of the key in the bucket, or -1; identical on
+// all lanes of a group.
+template <int G, bool CG>
+__device__ __forceinline__ int probe_bucket(const TableDev& t, uint64_t b, uint64_t key,
+                                            uint32_t pat4, bool active, int lane_g,
+                                            unsigned group_bits, int group_base) {
+  int my = -1;
+  if (active) {
+    uint32_t w[32 / G];
+    load_line<G, CG>(t.digests + b * kSlots, lane_g, w);
+    const uint64_t* kb = t.keys + b * kSlots;
+#pragma unroll
+    for (int q = 0; q < 32 / G; ++q) {
+      uint32_t m = match4(w[q], pat4);
+      while (m) {
+        int bit = __ffs(m) - 1;
+        int slot = lane_g * (128 / G) + q * 4 + (bit >> 3);
+        uint64_t k = CG ? __ldcg(kb + slot) : __ldg(kb + slot);
+        if (k == key) my = slot;
+        m &= ~(0xFFu << (bit & ~7));
+      }
+    }
+  }
+  unsigned bal = __ballot_sync(0xFFFFFFFFu, my >= 0) & group_bits;
+  int src = bal ? __ffs(bal) - 1 : group_base;
+  int slot = __shfl_sync(0xFFFFFFFFu, my, src);
+  return bal ? slot : -1;
+}
+
+// Copy one value row of `dim` floats with G cooperating lanes, using 16-byte
+// vectors when VEC16 (dim % 4 == 0 and 16-byte aligned rows), else 4-byte.
+template <int G, bool VEC16, bool STREAM_DST>
+__device__ __forceinline__ void copy_row(float* dst, const float* src, uint32_t dim, int lane_g) {
+  if constexpr (VEC16) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    uint32_t n4 = dim >> 2;
+    for (uint32_t j = lane_g; j < n4; j += G) {
+      float4 v = __ldg(s4 + j);
+      if (STREAM_DST) __stcs(d4 + j, v); else d4[j] = v;
+    }
+  } else {
+    for (uint32_t j = lane_g; j < dim; j += G) {
+      float v = __ldg(src + j);
+      if (STREAM_DST) __stcs(dst + j, v); else dst[j] = v;
+    }
+  }
+}
+
+}  // namespace hkv

@@ -1,0 +1,108 @@
+// find / contains: digest-probe kernels (Algorithm 1, Sec. 3.2; reader
+// group of Sec. 3.5).
+//
+// A group of G lanes serves one key: every lane loads 128/G bytes of the
+// bucket's digest line (16-byte vector loads for G <= 8, so one group issues
+// exactly one 128-byte line), compares them four at a time with __vcmpeq4,
+// confirms each digest match against the full key, and the group agrees on
+// the hit through one warp ballot. The hit's value row is then copied by the
+// same G lanes with 16-byte loads and streaming stores. Dual-bucket tables
+// read the second line only when the first bucket missed.
+#include "hkv_internal.h"
+
+namespace hkv {
+namespace {
+
+constexpr int kFindThreads = 256;
+
+template <int G, bool VEC16, bool VALUES>
+__global__ void __launch_bounds__(kFindThreads)
+    find_kernel(TableDev t, uint64_t n, const uint64_t* __restrict__ keys,
+                float* __restrict__ out, uint8_t* __restrict__ found,
+                uint64_t* __restrict__ scores_out) {
+  constexpr int KPW = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int lane_g = lane & (G - 1);
+  const int group_base = lane & ~(G - 1);
+  const unsigned group_bits = G == 32 ? 0xFFFFFFFFu : (((1u << G) - 1u) << group_base);
+  const uint64_t warp = (blockIdx.x * (uint64_t)kFindThreads + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * kFindThreads) >> 5;
+  unsigned hits = 0, misses = 0;
+
+  for (uint64_t base = warp * KPW; base < n; base += nwarps * KPW) {
+    const uint64_t i = base + (lane / G);
+    bool in = i < n;
+    uint64_t key = in ? __ldg(keys + i) : kEmptyKey;
+    bool active = in && key < kFirstReserved;
+    uint64_t h = fmix64(key);
+    uint64_t b = h & t.bucket_mask;
+    uint32_t pat4 = digest_from_hash(h) * 0x01010101u;
+    int slot = probe_bucket<G, false>(t, b, key, pat4, active, lane_g, group_bits, group_base);
+    if (t.dual) {
+      uint64_t b2 = second_bucket(t, key);
+      bool need = active && slot < 0 && b2 != b;
+      if (__any_sync(0xFFFFFFFFu, need)) {
+        int s2 = probe_bucket<G, false>(t, b2, key, pat4, need, lane_g, group_bits, group_base);
+        if (need && s2 >= 0) {
+          slot = s2;
+          b = b2;
+        }
+      }
+    }
+    const bool hit = active && slot >= 0;
+    if (hit) {
+      const uint64_t g = b * kSlots + (uint64_t)slot;
+      if (VALUES) copy_row<G, VEC16, true>(out + i * t.dim, value_ptr(t, g), t.dim, lane_g);
+      if (scores_out && lane_g == 0) scores_out[i] = __ldg(t.scores + g);
+    }
+    if (in && lane_g == 0) {
+      if (found) found[i] = hit ? 1 : 0;
+      hits += hit;
+      misses += !hit;
+    }
+  }
+  hits = __reduce_add_sync(0xFFFFFFFFu, hits);
+  misses = __reduce_add_sync(0xFFFFFFFFu, misses);
+  if (lane == 0) {
+    count_add(t, HKV_CNT_FIND_HIT, hits);
+    count_add(t, HKV_CNT_FIND_MISS, misses);
+  }
+}
+
+template <int G>
+void launch_g(const hkv_table_s* t, uint64_t n, const uint64_t* keys, float* out, uint8_t* found,
+              uint64_t* scores_out, bool vec16, cudaStream_t s) {
+  uint64_t warps_needed = (n + (32 / G) - 1) / (32 / G);
+  uint64_t blocks = (warps_needed * 32 + kFindThreads - 1) / kFindThreads;
+  uint64_t cap = (uint64_t)t->num_sms * (2048 / kFindThreads);
+  if (blocks > cap) blocks = cap;
+  if (blocks == 0) blocks = 1;
+  if (!out)
+    find_kernel<G, false, false><<<(unsigned)blocks, kFindThreads, 0, s>>>(t->dev, n, keys, out,
+                                                                           found, scores_out);
+  else if (vec16)
+    find_kernel<G, true, true><<<(unsigned)blocks, kFindThreads, 0, s>>>(t->dev, n, keys, out,
+                                                                         found, scores_out);
+  else
+    find_kernel<G, false, true><<<(unsigned)blocks, kFindThreads, 0, s>>>(t->dev, n, keys, out,
+                                                                          found, scores_out);
+}
+
+}  // namespace
+
+hkv_status launch_find(hkv_table_s* t, uint64_t n, const uint64_t* keys, float* values_out,
+                       uint8_t* found, uint64_t* scores_out, cudaStream_t s) {
+  if (n == 0) return HKV_OK;
+  bool vec16 = (t->dev.dim % 4 == 0) && ((reinterpret_cast<uintptr_t>(values_out) & 15) == 0);
+  switch (t->launch.find_tpk) {
+    case 1: launch_g<1>(t, n, keys, values_out, found, scores_out, vec16, s); break;
+    case 2: launch_g<2>(t, n, keys, values_out, found, scores_out, vec16, s); break;
+    case 4: launch_g<4>(t, n, keys, values_out, found, scores_out, vec16, s); break;
+    case 16: launch_g<16>(t, n, keys, values_out, found, scores_out, vec16, s); break;
+    case 32: launch_g<32>(t, n, keys, values_out, found, scores_out, vec16, s); break;
+    default: launch_g<8>(t, n, keys, values_out, found, scores_out, vec16, s); break;
+  }
+  return cuda_status(cudaGetLastError(), "find launch");
+}
+
+}  // namespace hkv

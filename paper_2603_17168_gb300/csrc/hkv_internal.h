@@ -1,0 +1,90 @@
+// Host-side table object and the internal launchers shared by the
+// translation units of the library (no scheduling inside the launchers; the
+// C-ABI entry points wrap them in the triple-group scheduler).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "hkv_common.cuh"
+#include "sched.hpp"
+
+namespace hkv {
+
+// CUDA-event backend of the triple-group scheduler.
+struct CudaEvents {
+  using Stream = cudaStream_t;
+  using Event = cudaEvent_t;
+  std::vector<cudaEvent_t> pool;
+  Event record(Stream s) {
+    cudaEvent_t e;
+    if (pool.empty()) {
+      cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    } else {
+      e = pool.back();
+      pool.pop_back();
+    }
+    cudaEventRecord(e, s);
+    return e;
+  }
+  void wait(Stream s, Event e) { cudaStreamWaitEvent(s, e, 0); }
+  bool same(Stream a, Stream b) const { return a == b; }
+  void recycle(Event e) { pool.push_back(e); }
+  ~CudaEvents() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+// Launch shape chosen for the probe kernels.
+struct LaunchCfg {
+  int find_tpk = 8;    // threads per key, find / contains
+  int update_tpk = 8;  // threads per key, update phase of upsert / assign
+};
+
+}  // namespace hkv
+
+struct hkv_table_s {
+  hkv::TableDev dev{};
+  hkv_options opts{};
+  int device = 0;
+  int num_sms = 0;
+  uint64_t num_buckets = 0;
+  uint64_t capacity = 0;
+  uint64_t slots_per_slice = 0;
+  uint64_t hbm_value_slots = 0;
+  uint64_t step = 0;
+  uint64_t epoch = 0;
+  hkv::LaunchCfg launch;
+  void* meta = nullptr;                 // digests + keys + scores + err + counters
+  std::vector<void*> hbm_slices;
+  std::vector<void*> host_slices;
+  float** slices_dev = nullptr;
+  cudaMemPool_t pool = nullptr;         // stream-ordered scratch allocations
+  hkv::TripleGroup<hkv::CudaEvents> sched;
+};
+
+namespace hkv {
+
+void set_last_error(const std::string& msg);
+hkv_status cuda_status(cudaError_t e, const char* what);
+
+// Raw launchers (asynchronous on `s`); each returns HKV_OK or an error after
+// checking its launches.
+hkv_status launch_find(hkv_table_s* t, uint64_t n, const uint64_t* keys, float* values_out,
+                       uint8_t* found, uint64_t* scores_out, cudaStream_t s);
+hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,
+                         const uint64_t* scores, uint8_t* status_out, uint64_t* ev_keys,
+                         uint64_t* ev_scores, float* ev_values, uint64_t* n_evicted,
+                         ScoreCtx ctx, cudaStream_t s);
+hkv_status launch_assign(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,
+                         const uint64_t* scores, ScoreCtx ctx, cudaStream_t s);
+hkv_status launch_erase(hkv_table_s* t, uint64_t n, const uint64_t* keys, cudaStream_t s);
+hkv_status launch_export(hkv_table_s* t, uint64_t offset, uint64_t n_slots, uint64_t* count_out,
+                         uint64_t* keys, float* values, uint64_t* scores, uint64_t* slots,
+                         cudaStream_t s);
+hkv_status launch_size(hkv_table_s* t, unsigned long long* out_dev, cudaStream_t s);
+
+}  // namespace hkv

@@ -1,0 +1,432 @@
+// Table lifecycle, size / export kernels and the C-ABI entry points.
+//
+// Storage (Sec. 4.2, "Tiered Storage Engine"): the digest, key and score
+// arrays always sit in HBM, in one allocation. Values are cut into slices of
+// a power-of-two number of whole buckets; slices are taken from HBM while the
+// value budget lasts, then from pinned host memory mapped into the device
+// address space (cudaHostAllocMapped), so kernels reach both through the
+// same position-based address and no CPU thread is on the data path.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "hkv_internal.h"
+
+namespace hkv {
+
+namespace {
+thread_local std::string g_last_error;
+
+constexpr uint64_t kDefaultSlice = 1ull << 30;
+
+__global__ void init_meta_kernel(uint8_t* digests, uint64_t* keys, uint64_t* scores,
+                                 uint64_t slots) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < slots;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    keys[i] = kEmptyKey;
+    scores[i] = 0;
+    if ((i & 15) == 0) reinterpret_cast<uint4*>(digests)[i >> 4] = make_uint4(0, 0, 0, 0);
+  }
+}
+
+// Occupied slots = non-zero digest bytes, 16 per thread per step.
+__global__ void size_kernel(const uint8_t* __restrict__ digests, uint64_t n16,
+                            unsigned long long* out) {
+  unsigned long long c = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n16;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint4 v = __ldg(reinterpret_cast<const uint4*>(digests) + i);
+    c += 16 - ((__popc(__vcmpeq4(v.x, 0)) + __popc(__vcmpeq4(v.y, 0)) + __popc(__vcmpeq4(v.z, 0)) +
+                __popc(__vcmpeq4(v.w, 0))) >> 3);
+  }
+  c = __reduce_add_sync(0xFFFFFFFFu, (unsigned)c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+// One warp per 32 consecutive slots: the ballot compacts the occupied ones,
+// then the warp copies their value rows cooperatively.
+__global__ void export_kernel(TableDev t, uint64_t offset, uint64_t n_slots,
+                              unsigned long long* count, uint64_t* __restrict__ keys,
+                              float* __restrict__ values, uint64_t* __restrict__ scores,
+                              uint64_t* __restrict__ slots) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t base = warp * 32; base < n_slots; base += nwarps * 32) {
+    const uint64_t g = offset + base + lane;
+    const bool in = base + lane < n_slots;
+    const uint64_t k = in ? t.keys[g] : kEmptyKey;
+    const bool occ = in && k < kLockedKey;
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, occ);
+    if (!bal) continue;
+    unsigned long long o0 = 0;
+    if (lane == 0) o0 = atomicAdd(count, (unsigned long long)__popc(bal));
+    o0 = __shfl_sync(0xFFFFFFFFu, o0, 0);
+    if (occ) {
+      const unsigned long long o = o0 + __popc(bal & ((1u << lane) - 1u));
+      if (keys) keys[o] = k;
+      if (scores) scores[o] = t.scores[g];
+      if (slots) slots[o] = g;
+    }
+    if (values) {
+      unsigned rest = bal;
+      for (int r = 0; rest; ++r) {
+        const int src_lane = __ffs(rest) - 1;
+        rest &= rest - 1;
+        const uint64_t gs = offset + base + src_lane;
+        const float* v = value_ptr(t, gs);
+        for (uint32_t d = lane; d < t.dim; d += 32) values[(o0 + r) * t.dim + d] = v[d];
+      }
+    }
+  }
+}
+
+hkv_status fail(hkv_status s, const std::string& msg) {
+  set_last_error(msg);
+  return s;
+}
+
+}  // namespace
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+hkv_status cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return HKV_OK;
+  set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? HKV_ERR_OOM : HKV_ERR_CUDA;
+}
+
+hkv_status launch_size(hkv_table_s* t, unsigned long long* out_dev, cudaStream_t s) {
+  cudaMemsetAsync(out_dev, 0, 8, s);
+  const uint64_t n16 = t->num_buckets * kSlots / 16;
+  uint64_t blocks = std::min<uint64_t>((n16 + 255) / 256, (uint64_t)t->num_sms * 8);
+  size_kernel<<<(unsigned)std::max<uint64_t>(blocks, 1), 256, 0, s>>>(t->dev.digests, n16, out_dev);
+  return cuda_status(cudaGetLastError(), "size launch");
+}
+
+hkv_status launch_export(hkv_table_s* t, uint64_t offset, uint64_t n_slots, uint64_t* count_out,
+                         uint64_t* keys, float* values, uint64_t* scores, uint64_t* slots,
+                         cudaStream_t s) {
+  cudaMemsetAsync(count_out, 0, 8, s);
+  if (n_slots == 0) return cuda_status(cudaGetLastError(), "export");
+  uint64_t blocks = std::min<uint64_t>((n_slots + 255) / 256, (uint64_t)t->num_sms * 8);
+  export_kernel<<<(unsigned)std::max<uint64_t>(blocks, 1), 256, 0, s>>>(
+      t->dev, offset, n_slots, reinterpret_cast<unsigned long long*>(count_out), keys, values,
+      scores, slots);
+  return cuda_status(cudaGetLastError(), "export launch");
+}
+
+}  // namespace hkv
+
+using namespace hkv;
+
+namespace {
+
+void free_table(hkv_table_s* t) {
+  for (void* p : t->hbm_slices) cudaFree(p);
+  for (void* p : t->host_slices) cudaFreeHost(p);
+  if (t->slices_dev) cudaFree(t->slices_dev);
+  if (t->meta) cudaFree(t->meta);
+  if (t->pool) cudaMemPoolDestroy(t->pool);
+  delete t;
+}
+
+// Latched device error, read and cleared (stream-ordered).
+hkv_status take_device_error(hkv_table_s* t, cudaStream_t s) {
+  uint32_t e = 0;
+  cudaError_t ce = cudaMemcpyAsync(&e, t->dev.err, 4, cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return cuda_status(ce, "sync");
+  if (e) {
+    cudaMemsetAsync(t->dev.err, 0, 4, s);
+    cudaStreamSynchronize(s);
+    const char* what = e == HKV_ERR_RESERVED_KEY    ? "a batch held a reserved key (>= 2^63)"
+                       : e == HKV_ERR_DUPLICATE_KEY ? "deterministic mode: a batch held a key twice"
+                       : e == HKV_ERR_TIMEOUT       ? "a bounded slot-claim wait ran out"
+                                                    : "device error";
+    set_last_error(what);
+    return (hkv_status)e;
+  }
+  return HKV_OK;
+}
+
+bool bad(hkv_table_t t) { return t == nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+const char* hkv_last_error(void) { return g_last_error.c_str(); }
+
+hkv_status hkv_create(const hkv_options* o, hkv_table_t* out) {
+  if (!o || !out) return fail(HKV_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (o->dim == 0 || o->capacity == 0 || o->policy < HKV_LRU || o->policy > HKV_CUSTOM_TS_FREQ)
+    return fail(HKV_ERR_INVALID_ARG, "capacity, dim and policy must be valid");
+  uint64_t nb = 1;
+  while (nb * kSlots < o->capacity) nb <<= 1;
+  if (nb > (1ull << 32)) return fail(HKV_ERR_INVALID_ARG, "capacity above 2^39 slots");
+
+  hkv_table_s* t = new hkv_table_s();
+  t->opts = *o;
+  t->num_buckets = nb;
+  t->capacity = nb * kSlots;
+  cudaGetDevice(&t->device);
+  cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, t->device);
+  const uint64_t slots = t->capacity;
+  const uint64_t dim = o->dim;
+
+  // metadata: digests | keys | scores | err | counters
+  const uint64_t off_keys = slots;                    // digests: slots bytes (multiple of 128)
+  const uint64_t off_scores = off_keys + slots * 8;
+  const uint64_t off_err = off_scores + slots * 8;
+  const uint64_t off_cnt = off_err + 256;
+  const uint64_t meta_bytes = off_cnt + 256;
+  cudaError_t e = cudaMalloc(&t->meta, meta_bytes);
+  if (e != cudaSuccess) {
+    free_table(t);
+    return cuda_status(e, "metadata allocation");
+  }
+  char* m = static_cast<char*>(t->meta);
+  t->dev.digests = reinterpret_cast<uint8_t*>(m);
+  t->dev.keys = reinterpret_cast<uint64_t*>(m + off_keys);
+  t->dev.scores = reinterpret_cast<uint64_t*>(m + off_scores);
+  t->dev.err = reinterpret_cast<uint32_t*>(m + off_err);
+  t->dev.counters = reinterpret_cast<unsigned long long*>(m + off_cnt);
+  t->dev.bucket_mask = nb - 1;
+  t->dev.dim = o->dim;
+  t->dev.policy = o->policy;
+  t->dev.dual = o->dual_bucket ? 1 : 0;
+
+  // value slices: a power-of-two number of buckets each
+  const uint64_t want_slice = o->slice_bytes ? o->slice_bytes : kDefaultSlice;
+  uint64_t bps = 1;
+  while (bps * 2 <= nb && bps * 2 * kSlots * dim * 4 <= want_slice) bps <<= 1;
+  t->slots_per_slice = bps * kSlots;
+  int shift = 0;
+  while ((1ull << shift) < t->slots_per_slice) ++shift;
+  t->dev.slice_shift = (uint32_t)shift;
+  const uint64_t n_slices = nb / bps;
+  const uint64_t slice_bytes = t->slots_per_slice * dim * 4;
+  uint64_t budget = o->hbm_value_budget_bytes ? o->hbm_value_budget_bytes : ~0ull;
+  std::vector<float*> bases;
+  for (uint64_t i = 0; i < n_slices; ++i) {
+    void* p = nullptr;
+    if (budget >= slice_bytes) {
+      e = cudaMalloc(&p, slice_bytes);
+      if (e != cudaSuccess) break;
+      t->hbm_slices.push_back(p);
+      budget -= slice_bytes;
+      t->hbm_value_slots += t->slots_per_slice;
+    } else {
+      e = cudaHostAlloc(&p, slice_bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+      if (e != cudaSuccess) break;
+      t->host_slices.push_back(p);
+      void* dp = nullptr;
+      e = cudaHostGetDevicePointer(&dp, p, 0);
+      if (e != cudaSuccess) break;
+      p = dp;
+      budget = 0;
+    }
+    bases.push_back(static_cast<float*>(p));
+  }
+  if (e != cudaSuccess) {
+    free_table(t);
+    return cuda_status(e, "value slice allocation");
+  }
+  e = cudaMalloc(&t->slices_dev, n_slices * sizeof(float*));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(t->slices_dev, bases.data(), n_slices * sizeof(float*), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_table(t);
+    return cuda_status(e, "slice table");
+  }
+  t->dev.values0 = bases[0];
+  t->dev.slices = t->slices_dev;
+  for (size_t i = 0; i < t->hbm_slices.size(); ++i) cudaMemset(t->hbm_slices[i], 0, slice_bytes);
+
+  // stream-ordered pool for per-call scratch; keep freed blocks cached
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = t->device;
+  e = cudaMemPoolCreate(&t->pool, &props);
+  if (e == cudaSuccess) {
+    uint64_t keep = ~0ull;
+    e = cudaMemPoolSetAttribute(t->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  if (e != cudaSuccess) {
+    free_table(t);
+    return cuda_status(e, "scratch pool");
+  }
+
+  init_meta_kernel<<<std::max(1, t->num_sms * 8), 256>>>(t->dev.digests, t->dev.keys,
+                                                         t->dev.scores, slots);
+  cudaMemset(t->dev.err, 0, 256);
+  cudaMemset(t->dev.counters, 0, 256);
+  if (t->opts.dim >= 64) {
+    t->launch.find_tpk = 16;
+    t->launch.update_tpk = 16;
+  }
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_table(t);
+    return cuda_status(e, "table initialisation");
+  }
+  *out = t;
+  return HKV_OK;
+}
+
+hkv_status hkv_destroy(hkv_table_t t) {
+  if (bad(t)) return fail(HKV_ERR_INVALID_ARG, "null table");
+  cudaDeviceSynchronize();
+  t->sched.clear();
+  free_table(t);
+  return HKV_OK;
+}
+
+uint64_t hkv_capacity(hkv_table_t t) { return t ? t->capacity : 0; }
+uint64_t hkv_num_buckets(hkv_table_t t) { return t ? t->num_buckets : 0; }
+uint32_t hkv_dim(hkv_table_t t) { return t ? t->opts.dim : 0; }
+uint64_t hkv_hbm_value_slots(hkv_table_t t) { return t ? t->hbm_value_slots : 0; }
+
+hkv_status hkv_find(hkv_table_t t, uint64_t n, const uint64_t* keys, float* values_out,
+                    uint8_t* found, uint64_t* scores_out, hkv_stream_t stream) {
+  if (bad(t) || (n && (!keys || !values_out))) return fail(HKV_ERR_INVALID_ARG, "find arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto lk = t->sched.acquire(kReader, s);
+  hkv_status rc = launch_find(t, n, keys, values_out, found, scores_out, s);
+  t->sched.release(s);
+  return rc;
+}
+
+hkv_status hkv_contains(hkv_table_t t, uint64_t n, const uint64_t* keys, uint8_t* found,
+                        hkv_stream_t stream) {
+  if (bad(t) || (n && (!keys || !found))) return fail(HKV_ERR_INVALID_ARG, "contains arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto lk = t->sched.acquire(kReader, s);
+  hkv_status rc = launch_find(t, n, keys, nullptr, found, nullptr, s);
+  t->sched.release(s);
+  return rc;
+}
+
+hkv_status hkv_insert_or_assign(hkv_table_t t, uint64_t n, const uint64_t* keys,
+                                const float* values, const uint64_t* scores,
+                                uint8_t* status_out, uint64_t* evicted_keys,
+                                uint64_t* evicted_scores, float* evicted_values,
+                                uint64_t* n_evicted, hkv_stream_t stream) {
+  if (bad(t) || (n && (!keys || !values))) return fail(HKV_ERR_INVALID_ARG, "upsert arguments");
+  if (n && t->opts.policy == HKV_CUSTOM && !scores)
+    return fail(HKV_ERR_INVALID_ARG, "HKV_CUSTOM needs scores");
+  if (n >= (1ull << 31)) return fail(HKV_ERR_INVALID_ARG, "batch above 2^31 keys");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto lk = t->sched.acquire(kInserter, s);
+  ScoreCtx ctx{n ? t->step + 1 : t->step, t->epoch};
+  hkv_status rc = launch_upsert(t, n, keys, values,
+                                (t->opts.policy == HKV_CUSTOM) ? scores : nullptr, status_out,
+                                evicted_keys, evicted_scores, evicted_values, n_evicted, ctx, s);
+  if (rc == HKV_OK && n) t->step++;
+  t->sched.release(s);
+  return rc;
+}
+
+hkv_status hkv_assign(hkv_table_t t, uint64_t n, const uint64_t* keys, const float* values,
+                      const uint64_t* scores, hkv_stream_t stream) {
+  if (bad(t) || (n && !keys)) return fail(HKV_ERR_INVALID_ARG, "assign arguments");
+  if (n >= (1ull << 31)) return fail(HKV_ERR_INVALID_ARG, "batch above 2^31 keys");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto lk = t->sched.acquire(kUpdater, s);
+  ScoreCtx ctx{n ? t->step + 1 : t->step, t->epoch};
+  hkv_status rc = launch_assign(t, n, keys, values,
+                                (t->opts.policy == HKV_CUSTOM) ? scores : nullptr, ctx, s);
+  if (rc == HKV_OK && n) t->step++;
+  t->sched.release(s);
+  return rc;
+}
+
+hkv_status hkv_erase(hkv_table_t t, uint64_t n, const uint64_t* keys, hkv_stream_t stream) {
+  if (bad(t) || (n && !keys)) return fail(HKV_ERR_INVALID_ARG, "erase arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto lk = t->sched.acquire(kInserter, s);
+  hkv_status rc = launch_erase(t, n, keys, s);
+  t->sched.release(s);
+  return rc;
+}
+
+hkv_status hkv_size(hkv_table_t t, uint64_t* out, hkv_stream_t stream) {
+  if (bad(t) || !out) return fail(HKV_ERR_INVALID_ARG, "size arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long* d = t->dev.counters + 16;  // spare words after the counters
+  {
+    auto lk = t->sched.acquire(kReader, s);
+    hkv_status rc = launch_size(t, d, s);
+    t->sched.release(s);
+    if (rc) return rc;
+  }
+  unsigned long long h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e, "size");
+  *out = h;
+  return take_device_error(t, s);
+}
+
+hkv_status hkv_export_batch(hkv_table_t t, uint64_t slot_offset, uint64_t n_slots,
+                            uint64_t* count_out, uint64_t* keys, float* values, uint64_t* scores,
+                            uint64_t* slots, hkv_stream_t stream) {
+  if (bad(t) || !count_out) return fail(HKV_ERR_INVALID_ARG, "export arguments");
+  if (slot_offset > t->capacity || n_slots > t->capacity - slot_offset)
+    return fail(HKV_ERR_INVALID_ARG, "slot range outside the table");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto lk = t->sched.acquire(kReader, s);
+  hkv_status rc = launch_export(t, slot_offset, n_slots, count_out, keys, values, scores, slots, s);
+  t->sched.release(s);
+  return rc;
+}
+
+hkv_status hkv_set_step(hkv_table_t t, uint64_t step) {
+  if (bad(t)) return fail(HKV_ERR_INVALID_ARG, "null table");
+  t->step = step;
+  return HKV_OK;
+}
+
+uint64_t hkv_get_step(hkv_table_t t) { return t ? t->step : 0; }
+
+hkv_status hkv_set_epoch(hkv_table_t t, uint64_t epoch) {
+  if (bad(t)) return fail(HKV_ERR_INVALID_ARG, "null table");
+  t->epoch = epoch;
+  return HKV_OK;
+}
+
+hkv_status hkv_sync(hkv_table_t t, hkv_stream_t stream) {
+  if (bad(t)) return fail(HKV_ERR_INVALID_ARG, "null table");
+  return take_device_error(t, static_cast<cudaStream_t>(stream));
+}
+
+hkv_status hkv_read_counters(hkv_table_t t, uint64_t* out, hkv_stream_t stream) {
+  if (bad(t) || !out) return fail(HKV_ERR_INVALID_ARG, "counters arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(out, t->dev.counters, HKV_COUNTER_COUNT * 8,
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_status(e, "read counters");
+}
+
+hkv_status hkv_reset_counters(hkv_table_t t, hkv_stream_t stream) {
+  if (bad(t)) return fail(HKV_ERR_INVALID_ARG, "null table");
+  return cuda_status(cudaMemsetAsync(t->dev.counters, 0, HKV_COUNTER_COUNT * 8,
+                                     static_cast<cudaStream_t>(stream)),
+                     "reset counters");
+}
+
+hkv_status hkv_set_launch(hkv_table_t t, int find_tpk, int update_tpk) {
+  if (bad(t)) return fail(HKV_ERR_INVALID_ARG, "null table");
+  auto ok = [](int v) { return v == 0 || v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32; };
+  if (!ok(find_tpk) || !ok(update_tpk)) return fail(HKV_ERR_INVALID_ARG, "threads per key");
+  if (find_tpk) t->launch.find_tpk = find_tpk;
+  if (update_tpk) t->launch.update_tpk = update_tpk;
+  return HKV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,685 @@
+// insert_or_assign / assign / erase (Algorithms 2 and 3, Sec. 3.3-3.4;
+// updater and inserter groups of Sec. 3.5).
+//
+// A batch runs as a short pipeline on one stream:
+//   dedup     collapse duplicate keys (last occurrence's value, multiplicity
+//             m): per-block shared-memory hash aggregation, then a global
+//             open-addressing table, so a Zipf-hot key costs one global
+//             atomic per block instead of one per occurrence;
+//   update    phase U: probe every distinct key (G lanes per key, digest
+//             line + key confirm) and update residents in place; misses are
+//             appended to a compact list;
+//   insert    phase I: one warp per new key claims a free slot with a CAS
+//             on the key word (EMPTY -> LOCKED), or, when the bucket (both
+//             buckets in dual mode) is full, reduces the minimum (score, key)
+//             over the 128 (256) slots, applies admission control, CAS-locks
+//             the victim, re-validates its score under the lock and replaces
+//             it (Algorithm 2 lines 6-14, Algorithm 3);
+//   reconcile a victim that was itself inserted by this batch is not an
+//             eviction: its key becomes REJECTED and it is dropped from the
+//             evicted output;
+//   status    broadcast each distinct key's status to all its occurrences.
+// Phase U finishing before phase I starts is what makes the paper's claim
+// "no update races an eviction" hold for real batches.
+//
+// Single-bucket claims are linearisable (a slot's (score, key) only grows
+// while a bucket is full, and a victim is re-validated under its lock), and
+// any serial order of "insert if free, else replace the minimum iff larger"
+// ends with each bucket holding the largest 128 (score, key) pairs; so the
+// single-bucket result does not depend on the schedule.
+#include "hkv_internal.h"
+
+namespace hkv {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+struct DedupEntry {
+  unsigned long long key;   // kEmptyKey when unused
+  unsigned int nlast;       // ~(largest batch index of the key): atomicMin
+  unsigned int cnt_m1;      // multiplicity - 1 (starts at 0xFFFFFFFF)
+};
+static_assert(sizeof(DedupEntry) == 16, "dedup entry layout");
+
+enum : int { kCntUnique = 0, kCntMiss = 1, kCntEvRaw = 2, kCntEvOut = 3, kAbort = 4, kCntWords = 8 };
+
+struct Scratch {
+  DedupEntry* tab;
+  uint64_t tab_mask;
+  int tab_bits;
+  uint8_t* tstatus;          // [T] status per dedup entry
+  uint32_t* slot_of;         // [n] dedup entry of each batch position
+  uint32_t* ulist;           // [n] dedup entries of distinct keys
+  uint32_t* mlist;           // [n] dedup entries of keys that missed in phase U
+  unsigned long long* cnt;   // [kCntWords]
+  uint64_t* evk;             // [n] raw victims
+  uint64_t* evs;             // [n]
+  float* evv;                // [n][dim] or null
+};
+
+__device__ __forceinline__ uint64_t dedup_pos(uint64_t key, int bits) {
+  // top bits of a hash independent of the table's bucket bits
+  return fmix64(key ^ 0xD6E8FEB86659FD93ull) >> (64 - bits);
+}
+
+__device__ __forceinline__ bool aborted(const Scratch& s) {
+  return *reinterpret_cast<volatile unsigned long long*>(s.cnt + kAbort) != 0;
+}
+
+__device__ __forceinline__ void abort_batch(const Scratch& s, uint32_t* err, uint32_t code) {
+  latch_error(err, code);
+  atomicExch(s.cnt + kAbort, 1ull);
+}
+
+// Warp-aggregated append of `want` lanes to a list; returns each lane's slot.
+__device__ __forceinline__ unsigned long long warp_append(unsigned long long* counter, bool want) {
+  unsigned bal = __ballot_sync(kFull, want);
+  unsigned long long base = 0;
+  int lane = threadIdx.x & 31;
+  if (bal) {
+    int leader = __ffs(bal) - 1;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(bal));
+    base = __shfl_sync(kFull, base, leader);
+  }
+  return base + __popc(bal & ((1u << lane) - 1u));
+}
+
+// ------------------------------------------------------------------- dedup
+
+constexpr int kDedupThreads = 512;
+constexpr int kDedupKPT = 4;
+constexpr int kDedupTile = kDedupThreads * kDedupKPT;
+constexpr int kDedupSmemBits = 12;  // 4096 entries for a tile of 2048 keys
+constexpr int kDedupSmem = (1 << kDedupSmemBits) * (int)sizeof(DedupEntry);
+
+__global__ void __launch_bounds__(kDedupThreads)
+    dedup_kernel(uint64_t n, const uint64_t* __restrict__ keys, Scratch s, uint32_t* err,
+                 int deterministic, unsigned long long* uniq_counter) {
+  extern __shared__ DedupEntry sm[];
+  constexpr uint32_t kMask = (1u << kDedupSmemBits) - 1;
+  for (int p = threadIdx.x; p < (1 << kDedupSmemBits); p += kDedupThreads) {
+    sm[p].key = kEmptyKey;
+    sm[p].nlast = 0xFFFFFFFFu;
+    sm[p].cnt_m1 = 0xFFFFFFFFu;
+  }
+  __syncthreads();
+  const uint64_t tile0 = (uint64_t)blockIdx.x * kDedupTile;
+  int pos[kDedupKPT];
+#pragma unroll
+  for (int j = 0; j < kDedupKPT; ++j) {
+    pos[j] = -1;
+    uint64_t idx = tile0 + (uint64_t)j * kDedupThreads + threadIdx.x;
+    if (idx >= n) continue;
+    uint64_t k = __ldg(keys + idx);
+    if (k >= kFirstReserved) {
+      abort_batch(s, err, HKV_ERR_RESERVED_KEY);
+      continue;
+    }
+    uint32_t p = (uint32_t)dedup_pos(k, kDedupSmemBits);
+    for (;;) {  // at most 2048 distinct keys in 4096 entries: terminates
+      unsigned long long old = atomicCAS(&sm[p].key, kEmptyKey, (unsigned long long)k);
+      if (old == kEmptyKey || old == k) break;
+      p = (p + 1) & kMask;
+    }
+    atomicMin(&sm[p].nlast, ~(uint32_t)idx);
+    atomicAdd(&sm[p].cnt_m1, 1u);
+    pos[j] = (int)p;
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < (1 << kDedupSmemBits); p += kDedupThreads) {
+    unsigned long long k = sm[p].key;
+    bool have = k != kEmptyKey;
+    bool first = false;
+    uint64_t gp = 0;
+    if (have) {
+      uint32_t c = sm[p].cnt_m1 + 1u;
+      gp = dedup_pos(k, s.tab_bits);
+      for (;;) {  // table holds >= 2n entries: terminates
+        unsigned long long old = atomicCAS(&s.tab[gp].key, kEmptyKey, k);
+        if (old == kEmptyKey) { first = true; break; }
+        if (old == k) break;
+        gp = (gp + 1) & s.tab_mask;
+      }
+      atomicMin(&s.tab[gp].nlast, sm[p].nlast);
+      atomicAdd(&s.tab[gp].cnt_m1, c);
+      if (deterministic && (!first || c > 1)) abort_batch(s, err, HKV_ERR_DUPLICATE_KEY);
+    }
+    unsigned long long u = warp_append(uniq_counter, first);
+    if (first) s.ulist[u] = (uint32_t)gp;
+    if (have) sm[p].cnt_m1 = (uint32_t)gp;  // reuse: global entry of this key
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kDedupKPT; ++j) {
+    if (pos[j] < 0) continue;
+    uint64_t idx = tile0 + (uint64_t)j * kDedupThreads + threadIdx.x;
+    s.slot_of[idx] = sm[pos[j]].cnt_m1;
+  }
+}
+
+// ----------------------------------------------------------- phase U probe
+
+constexpr int kUpdThreads = 256;
+
+template <int G, bool VEC16, bool UPSERT>
+__global__ void __launch_bounds__(kUpdThreads)
+    update_kernel(TableDev t, Scratch s, const float* __restrict__ values,
+                  const uint64_t* __restrict__ scores_in, ScoreCtx ctx) {
+  if (aborted(s)) return;
+  constexpr int KPW = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int lane_g = lane & (G - 1);
+  const int group_base = lane & ~(G - 1);
+  const unsigned group_bits = G == 32 ? kFull : (((1u << G) - 1u) << group_base);
+  const uint64_t warp = (blockIdx.x * (uint64_t)kUpdThreads + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * kUpdThreads) >> 5;
+  const uint64_t nu = s.cnt[kCntUnique];
+  unsigned updated = 0;
+
+  for (uint64_t base = warp * KPW; base < nu; base += nwarps * KPW) {
+    const uint64_t u = base + (lane / G);
+    const bool active = u < nu;
+    uint32_t e = active ? s.ulist[u] : 0;
+    uint64_t key = active ? s.tab[e].key : kEmptyKey;
+    uint64_t h = fmix64(key);
+    uint64_t b = h & t.bucket_mask;
+    uint32_t pat4 = digest_from_hash(h) * 0x01010101u;
+    int slot = probe_bucket<G, false>(t, b, key, pat4, active, lane_g, group_bits, group_base);
+    if (t.dual) {
+      uint64_t b2 = second_bucket(t, key);
+      bool need = active && slot < 0 && b2 != b;
+      if (__any_sync(kFull, need)) {
+        int s2 = probe_bucket<G, false>(t, b2, key, pat4, need, lane_g, group_bits, group_base);
+        if (need && s2 >= 0) {
+          slot = s2;
+          b = b2;
+        }
+      }
+    }
+    const bool hit = active && slot >= 0;
+    if (hit) {
+      const uint64_t i = ~s.tab[e].nlast;
+      const uint64_t g = b * kSlots + (uint64_t)slot;
+      if (values) copy_row<G, VEC16, false>(value_ptr(t, g), values + i * t.dim, t.dim, lane_g);
+      if (lane_g == 0) {
+        uint64_t m = (uint64_t)s.tab[e].cnt_m1 + 1;
+        uint64_t old = t.scores[g];
+        t.scores[g] = policy_score(t.policy, true, old, m, scores_in != nullptr,
+                                   scores_in ? __ldg(scores_in + i) : 0, ctx);
+        s.tstatus[e] = HKV_ST_UPDATED;
+        updated++;
+      }
+    }
+    if (UPSERT) {
+      bool miss = active && !hit && lane_g == 0;
+      unsigned long long q = warp_append(s.cnt + kCntMiss, miss);
+      if (miss) s.mlist[q] = e;
+    }
+  }
+  updated = __reduce_add_sync(kFull, updated);
+  if (lane == 0) count_add(t, HKV_CNT_UPDATED, updated);
+}
+
+// --------------------------------------------------------- phase I insert
+
+constexpr int kInsThreads = 256;
+
+__device__ __forceinline__ unsigned long long shfl_min_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(kFull, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+
+// Write (key, value, score, digest) into a slot this warp holds LOCKED, then
+// publish the key. Values are written by all lanes; lane 0 owns the rest.
+template <bool VEC16>
+__device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_t key, uint64_t sc,
+                                          uint32_t dg, const float* src, int lane) {
+  float* dst = value_ptr(t, g);
+  if (VEC16) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (uint32_t j = lane; j < (t.dim >> 2); j += 32) __stcg(d4 + j, __ldg(s4 + j));
+  } else {
+    for (uint32_t j = lane; j < t.dim; j += 32) __stcg(dst + j, __ldg(src + j));
+  }
+  if (lane == 0) {
+    __stcg(t.scores + g, sc);
+    t.digests[g] = (uint8_t)dg;
+    __threadfence();
+    atomicExch(reinterpret_cast<unsigned long long*>(t.keys + g), (unsigned long long)key);
+  }
+  __syncwarp();
+}
+
+// Re-read the candidate slots (through L2) while holding slot `g` locked
+// with victim (smin, kmin); true iff no other slot precedes or ties it in
+// (score, key) order or is being rewritten. All lanes take part.
+__device__ __forceinline__ bool victim_is_min(const TableDev& t, uint64_t b1, uint64_t b2, bool two,
+                                              uint64_t g, unsigned long long smin,
+                                              unsigned long long kmin, int lane) {
+  bool bad = false;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    if (half == 1 && !two) break;
+    const uint64_t b = half ? b2 : b1;
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(t.scores + b * kSlots) + lane * 2;
+    const ulonglong2 a = __ldcg(p), c = __ldcg(p + 1);
+    const unsigned long long sv[4] = {a.x, a.y, c.x, c.y};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint64_t x = b * kSlots + lane * 4 + q;
+      if (x == g) {
+        bad |= sv[q] != smin;
+        continue;
+      }
+      if (sv[q] < smin) { bad = true; continue; }
+      if (sv[q] == smin) {
+        const uint64_t kx = __ldcg(t.keys + x);
+        bad |= kx == kLockedKey || kx < kmin;
+      }
+    }
+  }
+  return !__any_sync(kFull, bad);
+}
+
+template <bool VEC16>
+__global__ void __launch_bounds__(kInsThreads)
+    insert_kernel(TableDev t, Scratch s, const float* __restrict__ values,
+                  const uint64_t* __restrict__ scores_in, ScoreCtx ctx) {
+  if (aborted(s)) return;
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * (uint64_t)kInsThreads + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * kInsThreads) >> 5;
+  const uint64_t nm = s.cnt[kCntMiss];
+  unsigned inserted = 0, evicted = 0, rejected = 0, retries = 0;
+
+  for (uint64_t j = warp; j < nm; j += nwarps) {
+    const uint32_t e = s.mlist[j];
+    const uint64_t key = s.tab[e].key;
+    const uint64_t i = ~s.tab[e].nlast;
+    const uint64_t m = (uint64_t)s.tab[e].cnt_m1 + 1;
+    const uint64_t sc = policy_score(t.policy, false, 0, m, scores_in != nullptr,
+                                     scores_in ? __ldg(scores_in + i) : 0, ctx);
+    const float* src = values + i * t.dim;
+    const uint64_t h = fmix64(key);
+    const uint32_t dg = digest_from_hash(h);
+    const uint64_t b1 = h & t.bucket_mask;
+    const uint64_t b2 = t.dual ? second_bucket(t, key) : b1;
+    const bool two = b2 != b1;
+    uint8_t outcome = HKV_ST_REJECTED;
+    int attempt = 0;
+    for (; attempt < kMaxClaimAttempts; ++attempt) {
+      // back off with per-key jitter so warps colliding on a slot fall apart
+      if (attempt) __nanosleep((32u << (attempt < 6 ? attempt : 6)) + ((unsigned)(h >> 17) & 255u));
+      const uint32_t w1 = __ldcg(reinterpret_cast<const uint32_t*>(t.digests + b1 * kSlots) + lane);
+      const uint32_t z1 = __vcmpeq4(w1, 0u);
+      const int free1 = __reduce_add_sync(kFull, (unsigned)__popc(z1) >> 3);
+      uint32_t w2 = 0, z2 = 0;
+      int free2 = 0;
+      if (two) {
+        w2 = __ldcg(reinterpret_cast<const uint32_t*>(t.digests + b2 * kSlots) + lane);
+        z2 = __vcmpeq4(w2, 0u);
+        free2 = __reduce_add_sync(kFull, (unsigned)__popc(z2) >> 3);
+      }
+      if (free1 > 0 || free2 > 0) {
+        // Algorithm 2 lines 6-9 / Algorithm 3 phase D1: a free slot of the
+        // less occupied candidate (b1 on equal occupancy).
+        const bool use1 = !two || free1 >= free2;
+        const uint64_t bt = use1 ? b1 : b2;
+        const uint32_t zt = use1 ? z1 : z2;
+        const unsigned bal = __ballot_sync(kFull, zt != 0);
+        const unsigned r = (unsigned)(h >> 44) + (unsigned)attempt * 0x9E3779B9u;
+        const int pick = __fns(bal, 0, (int)(r % (unsigned)__popc(bal)) + 1);
+        int ok = 0;
+        uint64_t g = 0;
+        if (lane == pick) {
+          const int byte = (__ffs(zt) - 1) >> 3;
+          g = bt * kSlots + (uint64_t)(lane * 4 + byte);
+          ok = atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + g), kEmptyKey, kLockedKey) ==
+               kEmptyKey;
+        }
+        ok = __shfl_sync(kFull, ok, pick);
+        g = __shfl_sync(kFull, g, pick);
+        if (!ok) { retries++; continue; }
+        fill_slot<VEC16>(t, g, key, sc, dg, src, lane);
+        outcome = HKV_ST_INSERTED;
+        inserted++;
+        break;
+      }
+      // Full: minimum (score, key) over the candidate slots (Algorithm 2
+      // line 10; Algorithm 3 phase D2 takes both buckets' slots).
+      unsigned long long sv[8];
+      {
+        const ulonglong2* p1 = reinterpret_cast<const ulonglong2*>(t.scores + b1 * kSlots) + lane * 2;
+        ulonglong2 a = __ldcg(p1), c = __ldcg(p1 + 1);
+        sv[0] = a.x; sv[1] = a.y; sv[2] = c.x; sv[3] = c.y;
+        if (two) {
+          const ulonglong2* p2 = reinterpret_cast<const ulonglong2*>(t.scores + b2 * kSlots) + lane * 2;
+          ulonglong2 d = __ldcg(p2), f = __ldcg(p2 + 1);
+          sv[4] = d.x; sv[5] = d.y; sv[6] = f.x; sv[7] = f.y;
+        } else {
+          sv[4] = sv[5] = sv[6] = sv[7] = ~0ull;
+        }
+      }
+      unsigned long long lmin = sv[0];
+#pragma unroll
+      for (int q = 1; q < 8; ++q) lmin = sv[q] < lmin ? sv[q] : lmin;
+      const unsigned long long smin = shfl_min_u64(lmin);
+      // Tie-break by key among the slots holding the minimum score. A slot
+      // locked by another warp is mid-replacement and its next value is not
+      // known yet: re-read later rather than choose around it.
+      unsigned long long kbest = ~0ull;
+      int qbest = -1;
+      bool busy = false;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (q >= 4 && !two) break;
+        if (sv[q] != smin) continue;
+        const uint64_t bq = q < 4 ? b1 : b2;
+        const uint64_t kq = __ldcg(t.keys + bq * kSlots + lane * 4 + (q & 3));
+        if (kq >= kLockedKey) { busy = true; continue; }
+        if (kq < kbest) { kbest = kq; qbest = q; }
+      }
+      const unsigned long long kmin = shfl_min_u64(kbest);
+      if (__any_sync(kFull, busy) || kmin == ~0ull) { retries++; continue; }
+      // Admission control: admit iff (s, k) > (s_min, k_min).
+      if (!sk_less(smin, kmin, sc, key)) {
+        outcome = HKV_ST_REJECTED;
+        rejected++;
+        break;
+      }
+      const unsigned own = __ballot_sync(kFull, qbest >= 0 && kbest == kmin);
+      const int owner = __ffs(own) - 1;
+      int ok = 0;
+      uint64_t g = 0;
+      if (lane == owner) {
+        const uint64_t bq = qbest < 4 ? b1 : b2;
+        g = bq * kSlots + (uint64_t)(lane * 4 + (qbest & 3));
+        ok = atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + g), kmin, kLockedKey) == kmin;
+      }
+      ok = __shfl_sync(kFull, ok, owner);
+      g = __shfl_sync(kFull, g, owner);
+      if (!ok) { retries++; continue; }
+      // Validate under the lock that the victim is still the minimum of the
+      // candidate slots: its score unchanged, no other slot lower, no slot
+      // at the same score with a lower key or a replacement in flight. Slot
+      // values only grow while a bucket is full, so a victim that passes
+      // here is the minimum from now on: this is the claim's linearisation
+      // point.
+      if (!victim_is_min(t, b1, b2, two, g, smin, kmin, lane)) {
+        if (lane == owner) atomicExch(reinterpret_cast<unsigned long long*>(t.keys + g), kmin);
+        retries++;
+        continue;
+      }
+      unsigned long long q = 0;
+      if (lane == 0) {
+        q = atomicAdd(s.cnt + kCntEvRaw, 1ull);
+        s.evk[q] = kmin;
+        s.evs[q] = smin;
+      }
+      q = __shfl_sync(kFull, q, 0);
+      if (s.evv) {
+        const float* vsrc = value_ptr(t, g);
+        for (uint32_t d = lane; d < t.dim; d += 32) s.evv[q * t.dim + d] = __ldcg(vsrc + d);
+      }
+      fill_slot<VEC16>(t, g, key, sc, dg, src, lane);
+      outcome = HKV_ST_INSERTED;
+      evicted++;
+      break;
+    }
+    if (attempt == kMaxClaimAttempts && lane == 0) latch_error(t.err, HKV_ERR_TIMEOUT);
+    if (lane == 0) s.tstatus[e] = outcome;
+  }
+  if (lane == 0) {
+    count_add(t, HKV_CNT_INSERTED, inserted);
+    count_add(t, HKV_CNT_EVICTED, evicted);
+    count_add(t, HKV_CNT_REJECTED, rejected);
+    count_add(t, HKV_CNT_RETRIES, retries);
+  }
+}
+
+// --------------------------------------------------------------- reconcile
+
+__global__ void reconcile_kernel(TableDev t, Scratch s, uint64_t* __restrict__ ev_keys,
+                                 uint64_t* __restrict__ ev_scores, float* __restrict__ ev_values) {
+  if (aborted(s)) return;
+  const uint64_t nraw = s.cnt[kCntEvRaw];
+  for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < nraw;
+       q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = s.evk[q];
+    uint64_t gp = dedup_pos(k, s.tab_bits);
+    bool in_batch = false;
+    for (;;) {
+      const uint64_t tk = s.tab[gp].key;
+      if (tk == k) { in_batch = true; break; }
+      if (tk == kEmptyKey) break;
+      gp = (gp + 1) & s.tab_mask;
+    }
+    if (in_batch && s.tstatus[gp] == HKV_ST_INSERTED) {
+      s.tstatus[gp] = HKV_ST_REJECTED;  // displaced by a later key of this batch
+      continue;
+    }
+    const unsigned long long o = atomicAdd(s.cnt + kCntEvOut, 1ull);
+    if (ev_keys) ev_keys[o] = k;
+    if (ev_scores) ev_scores[o] = s.evs[q];
+    if (ev_values && s.evv)
+      for (uint32_t d = 0; d < t.dim; ++d) ev_values[o * t.dim + d] = s.evv[q * t.dim + d];
+  }
+}
+
+__global__ void status_kernel(uint64_t n, Scratch s, uint8_t* __restrict__ status_out,
+                              uint64_t* __restrict__ n_evicted) {
+  if (aborted(s)) return;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    if (status_out) status_out[i] = s.tstatus[s.slot_of[i]];
+  if (n_evicted && blockIdx.x == 0 && threadIdx.x == 0) *n_evicted = s.cnt[kCntEvOut];
+}
+
+// -------------------------------------------------------------------- erase
+
+__global__ void validate_kernel(uint64_t n, const uint64_t* __restrict__ keys, Scratch s,
+                                uint32_t* err) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    if (__ldg(keys + i) >= kFirstReserved) abort_batch(s, err, HKV_ERR_RESERVED_KEY);
+}
+
+template <int G>
+__global__ void __launch_bounds__(kUpdThreads)
+    erase_kernel(TableDev t, uint64_t n, const uint64_t* __restrict__ keys, Scratch s) {
+  if (aborted(s)) return;
+  constexpr int KPW = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int lane_g = lane & (G - 1);
+  const int group_base = lane & ~(G - 1);
+  const unsigned group_bits = G == 32 ? kFull : (((1u << G) - 1u) << group_base);
+  const uint64_t warp = (blockIdx.x * (uint64_t)kUpdThreads + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * kUpdThreads) >> 5;
+  for (uint64_t base = warp * KPW; base < n; base += nwarps * KPW) {
+    const uint64_t i = base + (lane / G);
+    const bool active = i < n;
+    const uint64_t key = active ? __ldg(keys + i) : kEmptyKey;
+    const uint64_t h = fmix64(key);
+    uint64_t b = h & t.bucket_mask;
+    const uint32_t pat4 = digest_from_hash(h) * 0x01010101u;
+    // Duplicates in the batch may clear the slot concurrently: read through L2.
+    int slot = probe_bucket<G, true>(t, b, key, pat4, active, lane_g, group_bits, group_base);
+    if (t.dual) {
+      const uint64_t b2 = second_bucket(t, key);
+      const bool need = active && slot < 0 && b2 != b;
+      if (__any_sync(kFull, need)) {
+        int s2 = probe_bucket<G, true>(t, b2, key, pat4, need, lane_g, group_bits, group_base);
+        if (need && s2 >= 0) { slot = s2; b = b2; }
+      }
+    }
+    if (active && slot >= 0 && lane_g == 0) {
+      const uint64_t g = b * kSlots + (uint64_t)slot;
+      t.digests[g] = 0;
+      t.keys[g] = kEmptyKey;
+      t.scores[g] = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- scratch
+
+struct ScratchAlloc {
+  Scratch s{};
+  void* base = nullptr;
+};
+
+uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+hkv_status alloc_scratch(hkv_table_s* t, uint64_t n, bool want_ev_values, cudaStream_t st,
+                         ScratchAlloc* a) {
+  int bits = 10;
+  while ((1ull << bits) < 2 * n) ++bits;
+  const uint64_t T = 1ull << bits;
+  const uint64_t sz_tab = align256(T * sizeof(DedupEntry));
+  const uint64_t sz_ts = align256(T);
+  const uint64_t sz_u32 = align256(n * 4);
+  const uint64_t sz_cnt = align256(kCntWords * 8);
+  const uint64_t sz_u64 = align256(n * 8);
+  const uint64_t sz_evv = want_ev_values ? align256(n * (uint64_t)t->dev.dim * 4) : 0;
+  const uint64_t total = sz_tab + sz_ts + 3 * sz_u32 + sz_cnt + 2 * sz_u64 + sz_evv;
+  cudaError_t e = cudaMallocFromPoolAsync(&a->base, total, t->pool, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error("scratch allocation failed");
+    return HKV_ERR_OOM;
+  }
+  char* p = static_cast<char*>(a->base);
+  Scratch& s = a->s;
+  s.tab = reinterpret_cast<DedupEntry*>(p); p += sz_tab;
+  s.tab_bits = bits;
+  s.tab_mask = T - 1;
+  s.tstatus = reinterpret_cast<uint8_t*>(p); p += sz_ts;
+  s.slot_of = reinterpret_cast<uint32_t*>(p); p += sz_u32;
+  s.ulist = reinterpret_cast<uint32_t*>(p); p += sz_u32;
+  s.mlist = reinterpret_cast<uint32_t*>(p); p += sz_u32;
+  s.cnt = reinterpret_cast<unsigned long long*>(p); p += sz_cnt;
+  s.evk = reinterpret_cast<uint64_t*>(p); p += sz_u64;
+  s.evs = reinterpret_cast<uint64_t*>(p); p += sz_u64;
+  s.evv = want_ev_values ? reinterpret_cast<float*>(p) : nullptr;
+  cudaMemsetAsync(s.tab, 0xFF, T * sizeof(DedupEntry), st);
+  cudaMemsetAsync(s.cnt, 0, kCntWords * 8, st);
+  return HKV_OK;
+}
+
+unsigned grid_for(const hkv_table_s* t, uint64_t threads_needed, int block, int per_sm) {
+  uint64_t blocks = (threads_needed + block - 1) / block;
+  uint64_t cap = (uint64_t)t->num_sms * per_sm;
+  if (blocks > cap) blocks = cap;
+  return blocks ? (unsigned)blocks : 1u;
+}
+
+template <int G, bool UPSERT>
+void launch_update_g(hkv_table_s* t, uint64_t n, const Scratch& s, const float* values,
+                     const uint64_t* scores, ScoreCtx ctx, bool vec16, cudaStream_t st) {
+  const unsigned grid = grid_for(t, n * G, kUpdThreads, 2048 / kUpdThreads);
+  if (vec16)
+    update_kernel<G, true, UPSERT><<<grid, kUpdThreads, 0, st>>>(t->dev, s, values, scores, ctx);
+  else
+    update_kernel<G, false, UPSERT><<<grid, kUpdThreads, 0, st>>>(t->dev, s, values, scores, ctx);
+}
+
+template <bool UPSERT>
+void launch_update(hkv_table_s* t, uint64_t n, const Scratch& s, const float* values,
+                   const uint64_t* scores, ScoreCtx ctx, bool vec16, cudaStream_t st) {
+  switch (t->launch.update_tpk) {
+    case 1: launch_update_g<1, UPSERT>(t, n, s, values, scores, ctx, vec16, st); break;
+    case 2: launch_update_g<2, UPSERT>(t, n, s, values, scores, ctx, vec16, st); break;
+    case 4: launch_update_g<4, UPSERT>(t, n, s, values, scores, ctx, vec16, st); break;
+    case 16: launch_update_g<16, UPSERT>(t, n, s, values, scores, ctx, vec16, st); break;
+    case 32: launch_update_g<32, UPSERT>(t, n, s, values, scores, ctx, vec16, st); break;
+    default: launch_update_g<8, UPSERT>(t, n, s, values, scores, ctx, vec16, st); break;
+  }
+}
+
+void launch_dedup(hkv_table_s* t, uint64_t n, const uint64_t* keys, const Scratch& s,
+                  cudaStream_t st) {
+  const unsigned grid = (unsigned)((n + kDedupTile - 1) / kDedupTile);
+  dedup_kernel<<<grid, kDedupThreads, kDedupSmem, st>>>(n, keys, s, t->dev.err,
+                                                        t->opts.deterministic, s.cnt + kCntUnique);
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+struct DedupSmemInit {
+  DedupSmemInit() {
+    cudaFuncSetAttribute(dedup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDedupSmem);
+  }
+};
+
+}  // namespace
+
+hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,
+                         const uint64_t* scores, uint8_t* status_out, uint64_t* ev_keys,
+                         uint64_t* ev_scores, float* ev_values, uint64_t* n_evicted,
+                         ScoreCtx ctx, cudaStream_t st) {
+  static DedupSmemInit init_once;
+  (void)init_once;
+  if (n == 0) {
+    if (n_evicted) cudaMemsetAsync(n_evicted, 0, 8, st);
+    return cuda_status(cudaGetLastError(), "upsert");
+  }
+  ScratchAlloc a;
+  hkv_status rc = alloc_scratch(t, n, ev_values != nullptr, st, &a);
+  if (rc) return rc;
+  const Scratch& s = a.s;
+  const bool vec16 = t->dev.dim % 4 == 0 && aligned16(values);
+  launch_dedup(t, n, keys, s, st);
+  launch_update<true>(t, n, s, values, scores, ctx, vec16, st);
+  const unsigned ig = grid_for(t, n * 32, kInsThreads, 2048 / kInsThreads);
+  if (vec16)
+    insert_kernel<true><<<ig, kInsThreads, 0, st>>>(t->dev, s, values, scores, ctx);
+  else
+    insert_kernel<false><<<ig, kInsThreads, 0, st>>>(t->dev, s, values, scores, ctx);
+  reconcile_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(t->dev, s, ev_keys, ev_scores,
+                                                            ev_values);
+  if (status_out || n_evicted)
+    status_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(n, s, status_out, n_evicted);
+  cudaFreeAsync(a.base, st);
+  return cuda_status(cudaGetLastError(), "insert_or_assign launch");
+}
+
+hkv_status launch_assign(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,
+                         const uint64_t* scores, ScoreCtx ctx, cudaStream_t st) {
+  static DedupSmemInit init_once;
+  (void)init_once;
+  if (n == 0) return HKV_OK;
+  ScratchAlloc a;
+  hkv_status rc = alloc_scratch(t, n, false, st, &a);
+  if (rc) return rc;
+  const bool vec16 = t->dev.dim % 4 == 0 && (values == nullptr || aligned16(values));
+  launch_dedup(t, n, keys, a.s, st);
+  launch_update<false>(t, n, a.s, values, scores, ctx, vec16, st);
+  cudaFreeAsync(a.base, st);
+  return cuda_status(cudaGetLastError(), "assign launch");
+}
+
+hkv_status launch_erase(hkv_table_s* t, uint64_t n, const uint64_t* keys, cudaStream_t st) {
+  if (n == 0) return HKV_OK;
+  // Only the abort word of the scratch block is used here.
+  void* base = nullptr;
+  if (cudaMallocFromPoolAsync(&base, 256, t->pool, st) != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error("scratch allocation failed");
+    return HKV_ERR_OOM;
+  }
+  Scratch s{};
+  s.cnt = static_cast<unsigned long long*>(base);
+  cudaMemsetAsync(s.cnt, 0, kCntWords * 8, st);
+  validate_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(n, keys, s, t->dev.err);
+  erase_kernel<8><<<grid_for(t, n * 8, kUpdThreads, 2048 / kUpdThreads), kUpdThreads, 0, st>>>(
+      t->dev, n, keys, s);
+  cudaFreeAsync(base, st);
+  return cuda_status(cudaGetLastError(), "erase launch");
+}
+
+}  // namespace hkv

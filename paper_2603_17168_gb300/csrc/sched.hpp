@@ -1,0 +1,92 @@
+// Triple-group concurrency control as a host-side scheduler over streams
+// (Sec. 3.5, Table 4; Sec. 4.4).
+//
+// The paper enforces "readers with readers, updaters with updaters, every
+// other pair exclusive" with host atomics mirrored to the device by a
+// one-thread propagation kernel. Here the same compatibility matrix becomes
+// stream-ordering: before an operation of group g is launched on stream s,
+// s waits on the completion events of every in-flight operation of a group
+// incompatible with g. No device-side spin is involved.
+//
+// State: the table is in an "epoch" of one group. While operations of that
+// group keep arriving (readers or updaters) they join the epoch: each waits
+// only for the frontier, the events of the previous epoch. An operation of a
+// different group, or any inserter (never compatible, not even with itself),
+// opens a new epoch whose frontier is every event of the current one.
+// Because each member of an epoch waited for the whole previous frontier,
+// waiting on the current epoch's events orders a newcomer after all earlier
+// incompatible work, transitively.
+//
+// Backend supplies: Stream, Event, Event record(Stream), void wait(Stream,
+// Event), bool same(Stream, Stream), void recycle(Event).
+#pragma once
+
+#include <mutex>
+#include <utility>
+#include <vector>
+
+namespace hkv {
+
+enum Group : int { kReader = 0, kUpdater = 1, kInserter = 2 };
+
+inline bool compatible(Group a, Group b) { return a == b && a != kInserter; }
+
+template <class Backend>
+class TripleGroup {
+ public:
+  using Stream = typename Backend::Stream;
+  using Event = typename Backend::Event;
+
+  explicit TripleGroup(Backend be = Backend()) : be_(std::move(be)) {}
+  ~TripleGroup() { clear(); }
+
+  // Order stream s after all in-flight work incompatible with group g.
+  // Call with the returned lock held until release().
+  std::unique_lock<std::mutex> acquire(Group g, Stream s) {
+    std::unique_lock<std::mutex> lk(mu_);
+    if (!(have_epoch_ && compatible(group_, g))) {
+      for (auto& fe : frontier_) be_.recycle(fe.second);
+      frontier_ = std::move(current_);
+      current_.clear();
+      group_ = g;
+      have_epoch_ = true;
+    }
+    for (auto& fe : frontier_)
+      if (!be_.same(fe.first, s)) be_.wait(s, fe.second);
+    return lk;
+  }
+
+  // Record the completion point of the operation just launched on s.
+  void release(Stream s) {
+    Event e = be_.record(s);
+    for (auto& ce : current_)
+      if (be_.same(ce.first, s)) {
+        be_.recycle(ce.second);
+        ce.second = e;
+        return;
+      }
+    current_.emplace_back(s, e);
+  }
+
+  // Drop every tracked event (the caller has synchronised the device).
+  void clear() {
+    std::lock_guard<std::mutex> lk(mu_);
+    for (auto& fe : frontier_) be_.recycle(fe.second);
+    for (auto& ce : current_) be_.recycle(ce.second);
+    frontier_.clear();
+    current_.clear();
+    have_epoch_ = false;
+  }
+
+  Backend& backend() { return be_; }
+
+ private:
+  Backend be_;
+  std::mutex mu_;
+  bool have_epoch_ = false;
+  Group group_ = kReader;
+  std::vector<std::pair<Stream, Event>> frontier_;
+  std::vector<std::pair<Stream, Event>> current_;
+};
+
+}  // namespace hkv

@@ -1,0 +1,334 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle on
+the same seeded inputs.
+
+Bars: single-bucket upsert and every find are bit-exact (table state as a
+sorted (key, score, value, bucket) multiset, statuses, evicted sets, hit
+masks, values and scores; values are stored, never computed, so no
+tolerance applies). Dual-bucket upsert is order-dependent under concurrency
+(phase D1 reads live occupancy): it must pass every invariant, keep the
+retained-key count within 0.1% of the oracle's, and find on its state must
+match the oracle loaded with that state bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_17168_gb300 import workloads as w
+from tests import invariants as inv
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2603_17168_gb300 as hkv  # noqa: E402
+from tests.gpu_util import NAN_BITS, dev, export_state, host, nan_filled, same_state  # noqa: E402
+
+
+def gpu_upsert(t, keys, vals, scores=None, want_values=True):
+    n = keys.size
+    st = torch.empty(n, dtype=torch.uint8, device="cuda")
+    ek = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
+    es = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
+    ev = torch.empty((max(n, 1), t.dim), dtype=torch.float32, device="cuda") if want_values else None
+    ne = torch.zeros(1, dtype=torch.int64, device="cuda")
+    t.insert_or_assign(dev(keys), dev(vals.reshape(n, t.dim)),
+                       None if scores is None else dev(scores), st, ek, es, ev, ne)
+    t.sync()
+    m = int(ne.item())
+    o = np.argsort(host(ek[:m]), kind="stable")
+    evv = host(ev[:m])[o] if want_values else None
+    return host(st), host(ek[:m])[o], host(es[:m])[o], evv
+
+
+def sorted_evicted(ek, es, ev):
+    o = np.argsort(ek, kind="stable")
+    return ek[o], es[o], ev[o]
+
+
+def compare_upsert(t, o, keys, vals, scores=None, deterministic=False):
+    ost, oek, oes, oev = o.insert_or_assign(keys, vals, scores, deterministic=deterministic)
+    gst, gek, ges, gev = gpu_upsert(t, keys, vals, scores)
+    assert np.array_equal(gst, ost), "statuses differ"
+    oek, oes, oev = sorted_evicted(oek, oes, oev)
+    assert np.array_equal(gek, oek) and np.array_equal(ges, oes), "evicted sets differ"
+    assert np.array_equal(gev.view(np.uint32), oev.view(np.uint32)), "evicted values differ"
+    return gst
+
+
+def compare_find(t, o, q):
+    n = q.size
+    out = nan_filled(n, t.dim)
+    found = torch.empty(n, dtype=torch.uint8, device="cuda")
+    sc = torch.zeros(n, dtype=torch.int64, device="cuda")
+    t.find(dev(q), out, found, sc)
+    torch.cuda.synchronize()
+    ov = np.zeros((n, t.dim), np.uint32)
+    ov[:] = NAN_BITS
+    ov = ov.view(np.float32)
+    ov, of, os_ = o.find(q, ov)
+    gf = host(found).astype(bool)
+    assert np.array_equal(gf, of), "hit masks differ"
+    assert np.array_equal(host(out).view(np.uint32), ov.view(np.uint32)), "values differ"
+    assert np.array_equal(host(sc)[gf], os_[of]), "scores differ"
+    assert np.array_equal(host(t.contains(dev(q))).astype(bool), of), "contains differs"
+    return gf
+
+
+def test_tiny_config_bit_exact():
+    """512 buckets x 128 slots, dim 8, LRU (score = step), deterministic,
+    16 batches of 4,096 distinct uniform keys (evictions from lambda ~ 0.7),
+    then 4,096 finds with exactly 50% hits."""
+    cfg = w.TINY
+    rng = np.random.default_rng(w.seed_for(1))
+    nb, dim = cfg["num_buckets"], cfg["dim"]
+    t = hkv.Table(nb * 128, dim, hkv.LRU, dual_bucket=False, deterministic=True)
+    o = oracle.OracleTable(nb, dim, oracle.LRU)
+    for _ in range(cfg["batches"]):
+        keys = w.uniform_keys(rng, cfg["batch"], distinct=True)
+        vals = w.normal_values(rng, keys.size, dim)
+        compare_upsert(t, o, keys, vals, deterministic=True)
+        same_state(export_state(t), o.export())
+        assert t.size() == o.size()
+    assert t.get_step() == o.step == 16
+    assert o.size() > 0.95 * nb * 128
+    resident = o.export()[0]
+    q = np.concatenate([rng.choice(resident, cfg["finds"] // 2, replace=False),
+                        w.uniform_keys(rng, cfg["finds"] // 2)])
+    rng.shuffle(q)
+    hits = compare_find(t, o, q)
+    assert hits.sum() == cfg["finds"] // 2
+
+
+@pytest.mark.parametrize("policy,dim", [(hkv.LFU, 16), (hkv.CUSTOM, 3), (hkv.CUSTOM_TS_FREQ, 4),
+                                        (hkv.EPOCH_LRU, 1), (hkv.EPOCH_LFU, 7), (hkv.LRU, 32)])
+def test_single_bucket_duplicates_bit_exact(policy, dim):
+    """Zipf batches full of duplicates, sizes spanning several dedup tiles
+    with ragged tails, plus the degenerate sizes 0 and 1."""
+    rng = np.random.default_rng(1000 + policy * 10 + dim)
+    nb = 64
+    t = hkv.Table(nb * 128, dim, policy)
+    o = oracle.OracleTable(nb, dim, policy)
+    z = w.Zipf(1.05, 30000)
+    for e, n in enumerate([5000, 1, 0, 2048, 7001, 3, 12000, 4096]):
+        t.set_epoch(e)
+        o.set_epoch(e)
+        keys = z.keys(rng, n)
+        vals = w.normal_values(rng, n, dim)
+        sc = rng.integers(0, 60, n, dtype=np.uint64) if policy == hkv.CUSTOM else None
+        compare_upsert(t, o, keys, vals, sc)
+        same_state(export_state(t), o.export())
+    q = np.concatenate([z.keys(rng, 3000), w.uniform_keys(rng, 1000)])
+    compare_find(t, o, q)
+
+
+def test_one_bucket_and_large_batch():
+    rng = np.random.default_rng(1100)
+    t = hkv.Table(1, 2, hkv.CUSTOM)               # rounds up to one bucket
+    assert t.capacity == 128 and t.num_buckets == 1
+    o = oracle.OracleTable(1, 2, oracle.CUSTOM)
+    for _ in range(5):
+        keys = w.uniform_keys(rng, 700, distinct=True)
+        compare_upsert(t, o, keys, w.normal_values(rng, 700, 2),
+                       rng.integers(0, 10**6, 700, dtype=np.uint64))
+        same_state(export_state(t), o.export())
+    # a batch four times the capacity of a 2^20-slot table
+    nb = 1 << 13
+    t2 = hkv.Table(nb * 128, 4, hkv.LRU)
+    o2 = oracle.OracleTable(nb, 4, oracle.LRU)
+    keys = w.uniform_keys(rng, 1 << 22)
+    compare_upsert(t2, o2, keys, w.normal_values(rng, keys.size, 4))
+    same_state(export_state(t2), o2.export())
+
+
+def test_assign_erase_and_reinsert_bit_exact():
+    rng = np.random.default_rng(1200)
+    nb, dim = 32, 8
+    for policy in (hkv.LFU, hkv.CUSTOM, hkv.LRU):
+        t = hkv.Table(nb * 128, dim, policy)
+        o = oracle.OracleTable(nb, dim, policy)
+        keys = w.uniform_keys(rng, 3000, distinct=True)
+        sc = rng.integers(0, 100, keys.size, dtype=np.uint64)
+        compare_upsert(t, o, keys, w.normal_values(rng, keys.size, dim), sc)
+        a = np.concatenate([keys[:500], keys[:100], w.uniform_keys(rng, 200)])
+        av = w.normal_values(rng, a.size, dim)
+        asc = rng.integers(0, 100, a.size, dtype=np.uint64)
+        t.assign(dev(a), dev(av), dev(asc))
+        o.assign(a, av, asc if policy == hkv.CUSTOM else None)
+        t.assign(dev(keys[500:600]), None, dev(asc[:100]))      # scores only
+        o.assign(keys[500:600], _current_values(o, keys[500:600]),
+                 asc[:100] if policy == hkv.CUSTOM else None)
+        same_state(export_state(t), o.export())
+        er = np.concatenate([keys[1000:1400], keys[1000:1010], w.uniform_keys(rng, 50)])
+        t.erase(dev(er))
+        o.erase(er)
+        same_state(export_state(t), o.export())
+        compare_upsert(t, o, keys[1000:1200], w.normal_values(rng, 200, dim), sc[:200])
+        same_state(export_state(t), o.export())
+        compare_find(t, o, np.concatenate([keys, er]))
+
+
+def _current_values(o, keys):
+    v, f, _ = o.find(keys)
+    return v
+
+
+def test_errors_leave_table_unchanged():
+    rng = np.random.default_rng(1300)
+    t = hkv.Table(16 * 128, 4, hkv.LRU, deterministic=True)
+    o = oracle.OracleTable(16, 4, oracle.LRU)
+    keys = w.uniform_keys(rng, 1000, distinct=True)
+    compare_upsert(t, o, keys, w.normal_values(rng, 1000, 4), deterministic=True)
+    before = export_state(t)
+    bad = keys.copy()
+    bad[500] = np.uint64(2**63 + 5)
+    with pytest.raises(hkv.HKVError) as e:
+        gpu_upsert(t, bad, w.normal_values(rng, 1000, 4))
+    assert e.value.code == 2
+    dup = np.concatenate([keys[:10], keys[:1]])
+    with pytest.raises(hkv.HKVError) as e:
+        gpu_upsert(t, dup, w.normal_values(rng, 11, 4))
+    assert e.value.code == 3
+    t.erase(dev(np.array([5, 2**64 - 1], np.uint64)))
+    with pytest.raises(hkv.HKVError):
+        t.sync()
+    same_state(export_state(t), before)
+    # empty batches are no-ops
+    gpu_upsert(t, np.zeros(0, np.uint64), np.zeros((0, 4), np.float32))
+    t.find(dev(np.zeros(0, np.uint64)))
+    t.assign(dev(np.zeros(0, np.uint64)))
+    t.erase(dev(np.zeros(0, np.uint64)))
+    same_state(export_state(t), before)
+    # a batch the device refuses still consumed its step number
+    assert t.get_step() == 3
+
+
+def _check_batch_invariants(t, nb, keys, st, ek, es):
+    """Invariants after one LFU batch: a new key's score is its multiplicity."""
+    gk, gs, gv, gb = export_state(t)
+    b1, b2, _ = oracle.map_keys(nb, True, gk)
+    inv.check_state(gk, gs, gb, nb, b1, b2, t.capacity)
+    uk, last, mult = np.unique(keys[::-1], return_index=True, return_counts=True)
+    last = keys.size - 1 - last
+    ust = st[last]
+    resident = np.isin(uk, gk)
+    assert np.all(resident[ust == hkv.ST_INSERTED])
+    assert not np.any(resident[ust == hkv.ST_REJECTED])
+    rej = uk[ust == hkv.ST_REJECTED]
+    rs = mult.astype(np.uint64)[ust == hkv.ST_REJECTED]
+    rb1, rb2, _ = oracle.map_keys(nb, True, rej)
+    eb1, eb2, _ = oracle.map_keys(nb, True, ek)
+    inv.check_admission(gk, gs, gb, nb, rej, rs, rb1, rb2, ek, es, eb1, eb2)
+    assert not np.any(np.isin(ek, gk)), "an evicted key is still resident"
+    return gk, gs, gv, gb
+
+
+def test_dual_bucket_invariants_count_and_find():
+    """Single-table shape at reduced size: 2^12 buckets, dim 32, LFU,
+    dual-bucket, uniform fill to lambda = 0.5 / 0.9 / 1.0, then Zipf(1.05)
+    batches over a 2^32 universe."""
+    rng = np.random.default_rng(w.seed_for(2))
+    nb, dim = 1 << 12, 32
+    t = hkv.Table(nb * 128, dim, hkv.LFU, dual_bucket=True)
+    o = oracle.OracleTable(nb, dim, oracle.LFU, True)
+    z = w.Zipf(1.05, 1 << 32)
+    cap = nb * 128
+    for lam in (0.5, 0.9, 1.0):
+        for _ in range(40):
+            if t.size() >= lam * cap * 0.999:
+                break
+            keys = w.uniform_keys(rng, 1 << 16, universe=1 << 32)
+            vals = w.normal_values(rng, keys.size, dim)
+            gst, gek, ges, _ = gpu_upsert(t, keys, vals)
+            o.insert_or_assign(keys, vals)
+            _check_batch_invariants(t, nb, keys, gst, gek, ges)
+        gs_, os_ = t.size(), o.size()
+        assert abs(gs_ - os_) <= 0.001 * os_, (lam, gs_, os_)
+        for _ in range(3):
+            keys = z.keys(rng, 1 << 17)
+            vals = w.normal_values(rng, keys.size, dim)
+            resident_before = set(export_state(t)[0].tolist())
+            gst, gek, ges, _ = gpu_upsert(t, keys, vals)
+            o.insert_or_assign(keys, vals)
+            gk, gs, gv, gb = _check_batch_invariants(t, nb, keys, gst, gek, ges)
+            assert set(gek.tolist()) <= resident_before, "evicted a key that was not resident"
+            # last value written wins
+            pos = {int(k): i for i, k in enumerate(keys.tolist())}
+            idx = np.searchsorted(gk, np.array(list(pos.keys()), np.uint64))
+            idx = np.clip(idx, 0, gk.size - 1)
+            for (k, i), j in zip(pos.items(), idx):
+                if gk[j] == k:
+                    assert gv[j].tobytes() == vals[i].tobytes()
+            gs_, os_ = t.size(), o.size()
+            assert abs(gs_ - os_) <= 0.001 * os_, (lam, gs_, os_)
+        # find on the GPU's own state vs the oracle loaded with it
+        gk, gs, gv, gb = export_state(t)
+        ref = oracle.OracleTable(nb, dim, oracle.LFU, True)
+        ref.load(gk, gs, gv, gb)
+        q = np.concatenate([z.keys(rng, 20000), w.uniform_keys(rng, 20000, universe=1 << 32)])
+        compare_find(t, ref, q)
+
+
+def test_tiered_values_in_host_memory():
+    """Values past a small HBM budget live in pinned mapped host slices; the
+    results are the same bit for bit."""
+    rng = np.random.default_rng(1400)
+    nb, dim = 128, 16
+    slice_bytes = 8 * 128 * dim * 4                       # 8 buckets per slice
+    t = hkv.Table(nb * 128, dim, hkv.LFU, hbm_value_budget_bytes=5 * slice_bytes,
+                  slice_bytes=slice_bytes)
+    assert t.hbm_value_slots == 5 * 8 * 128
+    o = oracle.OracleTable(nb, dim, oracle.LFU)
+    z = w.Zipf(0.99, 1 << 20)
+    for _ in range(6):
+        keys = z.keys(rng, 8000)
+        compare_upsert(t, o, keys, w.normal_values(rng, keys.size, dim))
+    same_state(export_state(t), o.export())
+    compare_find(t, o, z.keys(rng, 10000))
+
+
+def test_streams_follow_the_triple_group_order():
+    """An inserter on one stream and readers on others: each reader sees
+    exactly the batches issued before it (the scheduler inserts the waits)."""
+    rng = np.random.default_rng(1500)
+    nb, dim = 256, 32
+    t = hkv.Table(nb * 128, dim, hkv.LRU)
+    o = oracle.OracleTable(nb, dim, oracle.LRU)
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    pending = []
+    for r in range(6):
+        keys = w.uniform_keys(rng, 4096, distinct=True)
+        vals = w.normal_values(rng, 4096, dim)
+        kd, vd = dev(keys), dev(vals)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(streams[r % 3]):
+            t.insert_or_assign(kd, vd)
+        o.insert_or_assign(keys, vals)
+        q = np.concatenate([keys[:2000], w.uniform_keys(rng, 500)])
+        qd = dev(q)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(streams[(r + 1) % 3]):
+            out, found, _ = t.find(qd)
+        ov, of, _ = o.find(q)
+        pending.append((streams[(r + 1) % 3], out, found, ov, of))
+    torch.cuda.synchronize()
+    for s, out, found, ov, of in pending:
+        assert np.array_equal(host(found).astype(bool), of)
+        assert np.array_equal(host(out)[of].view(np.uint32), ov[of].view(np.uint32))
+
+
+def test_counters_account_for_every_key():
+    rng = np.random.default_rng(1600)
+    nb, dim = 64, 4
+    t = hkv.Table(nb * 128, dim, hkv.LFU)
+    keys = w.uniform_keys(rng, 12000, distinct=True)
+    t.reset_counters()
+    st, _, _, _ = gpu_upsert(t, keys, w.normal_values(rng, keys.size, dim))
+    c = t.read_counters()
+    assert c["updated"] == 0
+    assert c["inserted"] + c["evicted"] + c["rejected"] >= keys.size
+    t.find(dev(keys))
+    c = t.read_counters()
+    assert c["find_hit"] == int(np.sum(st == hkv.ST_INSERTED))
+    assert c["find_hit"] + c["find_miss"] == keys.size
