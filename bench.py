@@ -1,0 +1,570 @@
+#!/usr/bin/env python
+"""Throughput of the hash-table hot path on one GB300 (or N replicas).
+
+Workload (the single-table configuration): one table per load factor
+lambda in {0.50, 0.75, 0.90, 1.00}, each 2^26 slots (2^19 buckets x 128),
+value dim 32 fp32, LFU scores, dual-bucket selection, pre-filled with
+uniform keys over a 2^32-key universe; every step then runs, on each table,
+one find and one insert_or_assign of 1,048,576 Zipf(1.05) keys over the same
+universe through the plain one-batch-per-call path. A step is 8 calls and
+8 Mi keys; value = keys processed / second (B-KV/s), summed over ranks.
+
+`--impl reference` times the CPU oracle (oracle/, plain single-threaded C)
+on a bounded, scaled sample of the same workload instead.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "find / insert_or_assign B-KV/s at λ 0.50–1.00 (% HBM roofline); served p50/p99"
+UNIT = "B-KV/s"
+LAMBDAS = (0.50, 0.75, 0.90, 1.00)
+NB_LOG2 = 19
+DIM = 32
+BATCH = 1 << 20
+UNIVERSE = 1 << 32
+ALPHA = 1.05
+NOMINAL_HBM_GBS = 8000.0
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD = ("single table x4 (lambda 0.50/0.75/0.90/1.00): 2^26 slots (2^19 buckets x 128), "
+            "dim 32 fp32, LFU, dual-bucket, uniform fill over 2^32, per step find + "
+            "insert_or_assign of 2^20 Zipf(1.05) keys per table")
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--nb-log2", type=int, default=NB_LOG2, help="log2 buckets per table")
+    p.add_argument("--batch", type=int, default=BATCH)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--find-tpk", type=int, default=0)
+    p.add_argument("--update-tpk", type=int, default=0)
+    p.add_argument("--lambdas", type=str, default=",".join(str(x) for x in LAMBDAS),
+                   help="comma-separated load factors (a subset, for profiling runs)")
+    a = p.parse_args(argv)
+    a.lambdas = tuple(float(x) for x in a.lambdas.split(","))
+    return a
+
+
+# ------------------------------------------------------------- distribution
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def reduce_max_sum(ms: float, units: float, world: int, device=None):
+    """Max of elapsed ms and sum of units over ranks (replicas only)."""
+    if world <= 1:
+        return ms, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.samples = []
+        self.proc = None
+        self.dev = device_index
+        self.marks = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append((time.time(), parts))
+
+    def mark(self, name):
+        self.marks.append((name, time.time()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        def active(x):
+            return x.lower() in ("active", "0x1") or x.lower().startswith("active")
+        win = [p for (t, p) in self.samples if t0 - 0.25 <= t <= t1 + 0.25]
+        if not win:
+            win = [p for (_, p) in self.samples]
+        if not win:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        sm = [float(p[1]) for p in win if p[1].replace(".", "").isdigit()]
+        mx = [float(p[2]) for p in win if p[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for p in win for n, v in zip(names, p[5:9]) if active(v)})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(win),
+                "power_w_max": max((float(p[3]) for p in win
+                                    if p[3].replace(".", "").isdigit()), default=None)}
+
+
+# ----------------------------------------------------------------- roofline
+
+def load_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2603_17168_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel, workload_key):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken from the current kernel sources on this workload; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(workload_key, {}).get(kernel)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def kernel_bytes(kind: str, c: dict, n_calls: int, batch: int, dim: int) -> float:
+    """Algorithmic bytes a kernel kind had to move, from the device counters.
+    Coalesced streams count their exact bytes; each scattered scalar access
+    counts one 32-byte sector; a digest line is 128 B, a score line 1 KiB, a
+    value row 4*dim B (read and write counted separately)."""
+    D = 4 * dim
+    S = 32
+    if kind == "find":
+        return (n_calls * batch * 9 + 128 * c["find_lines"] + S * c["find_keys"]
+                + 2 * D * c["find_hit"])
+    u = c["unique"]
+    if kind == "update":
+        miss = u - c["updated"]
+        return (u * (4 + S) + 128 * c["upd_lines"] + S * c["upd_keys"]
+                + c["updated"] * (2 * D + 2 * S + S) + miss * 4)
+    if kind == "insert":
+        nm = c["inserted"] + c["evicted"] + c["rejected"]
+        claimed = c["inserted"] + c["evicted"]
+        return (nm * (4 + S + S) + 128 * c["ins_lines"] + 1024 * c["ins_score_lines"]
+                + S * c["ins_keys"] + claimed * (3 * S + 2 * D) + c["evicted"] * S)
+    if kind == "dedup":
+        return n_calls * batch * (8 + 4) + u * 2 * S
+    if kind == "status":
+        return n_calls * batch * (4 + 1 + S)
+    if kind == "reconcile":
+        return c["evicted"] * (16 + S)
+    return 0.0
+
+
+# -------------------------------------------------------------------- ours
+
+def fill_table(t, lam, gen, dim, batch_fill=1 << 20, max_batches=400):
+    import torch
+    from paper_2603_17168_gb300 import workloads as w
+    cap = t.capacity
+    target = lam * cap if lam < 1.0 else 0.999 * cap
+    vals = torch.randn((batch_fill, dim), device="cuda", generator=gen)
+    done = 0
+    est = int(lam * cap / batch_fill * 0.98)
+    for _ in range(max_batches):
+        k = w.uniform_keys_torch(gen, batch_fill, UNIVERSE)
+        if done >= est:
+            size = t.size()
+            if size >= target:
+                break
+            need = int(target - size)
+            if need < batch_fill and lam < 1.0:
+                k = k[:max(need, 1)].contiguous()
+        t.insert_or_assign(k, vals[:k.numel()])
+        done += 1
+    return t.size() / cap
+
+
+def run_ours(args):
+    import torch
+    import paper_2603_17168_gb300 as hkv
+    from paper_2603_17168_gb300 import workloads as w
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    nb = 1 << args.nb_log2
+    batch = args.batch
+    steps, warm = args.steps, args.warmup
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(w.seed_for(2, rank))
+
+    nvtx = torch.cuda.nvtx
+    lambdas = args.lambdas
+    tables, lam_fill = [], []
+    nvtx.range_push("fill")
+    for lam in lambdas:
+        t = hkv.Table(nb * 128, DIM, hkv.LFU, dual_bucket=True)
+        t.set_launch(args.find_tpk, args.update_tpk)
+        lam_fill.append(fill_table(t, lam, gen, DIM))
+        tables.append(t)
+    nvtx.range_pop()
+
+    z = w.Zipf(ALPHA, UNIVERSE)
+    nbat = warm + steps
+    fk = [w.zipf_keys_torch(gen, z, batch) for _ in range(nbat)]
+    uk = [w.zipf_keys_torch(gen, z, batch) for _ in range(nbat)]
+    uv = [torch.randn((batch, DIM), device=dev, generator=gen) for _ in range(nbat)]
+    out_v = torch.empty((batch, DIM), device=dev)
+    out_f = torch.empty(batch, dtype=torch.uint8, device=dev)
+    out_s = torch.empty(batch, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.6)
+
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in tables]
+          for _ in range(nbat)]
+
+    def step(i):
+        for li, t in enumerate(tables):
+            ev[i][li][0].record()
+            t.find(fk[i], out_v, out_f)
+            ev[i][li][1].record()
+            t.insert_or_assign(uk[i], uv[i], status_out=out_s)
+            ev[i][li][2].record()
+
+    nvtx.range_push("warmup")
+    for i in range(warm):
+        step(i)
+    torch.cuda.synchronize()
+    nvtx.range_pop()
+    lam_start = [t.size() / t.capacity for t in tables]
+    for t in tables:
+        t.reset_counters()
+        t.profile_read()
+        t.profile_enable(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nvtx.range_push("timed")
+    e0.record()
+    for i in range(warm, warm + steps):
+        step(i)
+    e1.record()
+    nvtx.range_pop()
+    e1.synchronize()
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    barrier(world)
+    ms_local = e0.elapsed_time(e1)
+    for t in tables:
+        t.profile_enable(False)
+        t.sync()
+    units_local = float(steps * len(tables) * 2 * batch)
+    ms, units = reduce_max_sum(ms_local, units_local, world, dev)
+    lam_end = [t.size() / t.capacity for t in tables]
+
+    # per-table, per-op times from the step events
+    per_lambda = []
+    for li, (lam, t) in enumerate(zip(lambdas, tables)):
+        f_ms = sum(ev[i][li][0].elapsed_time(ev[i][li][1]) for i in range(warm, warm + steps))
+        u_ms = sum(ev[i][li][1].elapsed_time(ev[i][li][2]) for i in range(warm, warm + steps))
+        c = t.read_counters()
+        per_lambda.append({
+            "lambda_target": lam, "lambda_fill": round(lam_fill[li], 4),
+            "lambda_start": round(lam_start[li], 4), "lambda_end": round(lam_end[li], 4),
+            "find_bkvs": round(steps * batch / f_ms / 1e6, 4),
+            "upsert_bkvs": round(steps * batch / u_ms / 1e6, 4),
+            "find_hit_rate": round(c["find_hit"] / max(1, c["find_hit"] + c["find_miss"]), 4),
+            "upsert_unique": c["unique"], "updated": c["updated"], "inserted": c["inserted"],
+            "evicted": c["evicted"], "rejected": c["rejected"], "retries": c["retries"],
+            "_counters": c})
+
+    # kernel-level roofline: device time per kernel kind from the library's
+    # event brackets on the launching stream, bytes from the counters
+    peak, peak_src = load_peak()
+    kinds = {}
+    for li, t in enumerate(tables):
+        prof = t.profile_read()
+        c = per_lambda[li]["_counters"]
+        for kind, (kms, launches) in prof.items():
+            e = kinds.setdefault(kind, {"ms": 0.0, "launches": 0, "bytes": 0.0})
+            e["ms"] += kms
+            e["launches"] += launches
+            e["bytes"] += kernel_bytes(kind, c, steps, batch, DIM)
+    for kind, e in kinds.items():
+        e["gbs"] = e["bytes"] / (e["ms"] * 1e6) if e["ms"] > 0 else None
+        e["frac_measured"] = e["gbs"] / peak if e["gbs"] else None
+        e["share"] = e["ms"] / sum(x["ms"] for x in kinds.values())
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    d = kinds[dom]
+    wkey = f"single_nb{args.nb_log2}_b{batch}_l{'-'.join(str(x) for x in lambdas)}"
+    traffic = traffic_for(dom, wkey)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(d["gbs"], 1), "peak": peak,
+                "unit": "GB/s", "frac": round(d["gbs"] / peak, 4),
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, copy, burst)",
+                "frac_of_nominal_8tbs": round(d["gbs"] / NOMINAL_HBM_GBS, 4),
+                "algorithmic_bytes_per_launch": round(d["bytes"] / d["launches"]),
+                "avg_launch_ms": round(d["ms"] / d["launches"], 5),
+                "traffic": traffic}
+    gpu_launches = sum(e["launches"] for e in kinds.values())
+    for e in per_lambda:
+        e.pop("_counters")
+
+    # end to end through the public API: pinned host inputs copied in and
+    # results copied out inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(tables, fk, uk, uv, warm, steps, batch, world, dev)
+    clk = clocks.summary(t_wall0, t_wall1)
+    clocks.stop()
+
+    result = None
+    if rank == 0:
+        value = units / (ms * 1e-3) / 1e9
+        result = {
+            "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": warm, "ms_per_step": round(ms / steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (seeded uniform fill + Zipf(1.05) request keys over 2^32, N(0,1) fp32 values)",
+            "config": {"workload": WORKLOAD, "buckets_per_table": nb, "slots_per_table": nb * 128,
+                       "dim": DIM, "batch": batch, "policy": "LFU", "dual_bucket": True,
+                       "lambdas": list(lambdas), "parallelism": f"replicas x{world}",
+                       "l2": "no flush: each table is 9.1 GiB and a step's inputs 1.1 GiB, "
+                             "both far above the 129 MB L2",
+                       "launch": {"find_tpk": args.find_tpk or "default",
+                                  "update_tpk": args.update_tpk or "default"}},
+            "per_lambda": per_lambda,
+            "kernels": {k: {"ms": round(v["ms"], 4), "launches": v["launches"],
+                            "share": round(v["share"], 4),
+                            "gbs": round(v["gbs"], 1) if v["gbs"] else None,
+                            "frac_measured": round(v["frac_measured"], 4) if v["frac_measured"] else None}
+                        for k, v in sorted(kinds.items(), key=lambda kv: -kv[1]["ms"])},
+            "roofline": roofline, "gpu_launches": gpu_launches, "clocks": clk, "e2e": e2e,
+        }
+    for t in tables:
+        t.close()
+    return result
+
+
+def run_e2e(tables, fk, uk, uv, warm, steps, batch, world, dev):
+    import torch
+    pin = lambda x: x.cpu().pin_memory()  # noqa: E731
+    fk_h = [pin(x) for x in fk]
+    uk_h = [pin(x) for x in uk]
+    uv_h = [pin(x) for x in uv]
+    kd = torch.empty(batch, dtype=torch.int64, device=dev)
+    ud = torch.empty(batch, dtype=torch.int64, device=dev)
+    vd = torch.empty((batch, DIM), device=dev)
+    out_v = torch.empty((batch, DIM), device=dev)
+    out_f = torch.empty(batch, dtype=torch.uint8, device=dev)
+    out_s = torch.empty(batch, dtype=torch.uint8, device=dev)
+    ov_h = torch.empty((batch, DIM)).pin_memory()
+    of_h = torch.empty(batch, dtype=torch.uint8).pin_memory()
+    os_h = torch.empty(batch, dtype=torch.uint8).pin_memory()
+    h2d = d2h = 0
+
+    def step(i, count):
+        nonlocal h2d, d2h
+        for t in tables:
+            kd.copy_(fk_h[i], non_blocking=True)
+            t.find(kd, out_v, out_f)
+            ov_h.copy_(out_v, non_blocking=True)
+            of_h.copy_(out_f, non_blocking=True)
+            ud.copy_(uk_h[i], non_blocking=True)
+            vd.copy_(uv_h[i], non_blocking=True)
+            t.insert_or_assign(ud, vd, status_out=out_s)
+            os_h.copy_(out_s, non_blocking=True)
+            if count:
+                h2d += kd.numel() * 8 + ud.numel() * 8 + vd.numel() * 4
+                d2h += ov_h.numel() * 4 + of_h.numel() + os_h.numel()
+
+    for i in range(warm):
+        step(i, False)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for i in range(warm, warm + steps):
+        step(i, True)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    barrier(world)
+    ms, units = reduce_max_sum((t1 - t0) * 1e3, float(steps * len(tables) * 2 * batch), world, dev)
+    return {"value": round(units / (ms * 1e-3) / 1e9, 4), "unit": UNIT,
+            "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
+            "ms_per_step": round(ms / steps, 4)}
+
+
+# -------------------------------------------------------------- the oracle
+
+SAMPLE_NB = 1 << 13        # 2^20 slots per table: 1/64 of the GPU tables
+SAMPLE_OPS = 1 << 16       # keys per find and per upsert call: 1/16 of a batch
+
+
+def oracle_tables(seed):
+    import oracle
+    from paper_2603_17168_gb300 import workloads as w
+    rng = np.random.default_rng(seed)
+    tabs = []
+    for lam in LAMBDAS:
+        t = oracle.OracleTable(SAMPLE_NB, DIM, oracle.LFU, True)
+        cap = t.capacity
+        target = lam * cap if lam < 1.0 else 0.999 * cap
+        vals = w.normal_values(rng, 1 << 16, DIM)
+        for _ in range(200):
+            size = t.size()
+            if size >= target:
+                break
+            n = int(min(1 << 16, max(1, target - size))) if lam < 1.0 else 1 << 16
+            t.insert_or_assign(w.uniform_keys(rng, n, universe=UNIVERSE), vals[:n])
+        tabs.append(t)
+    return tabs, rng
+
+
+def oracle_step(tabs, rng, z):
+    from paper_2603_17168_gb300 import workloads as w
+    fk = z.keys(rng, SAMPLE_OPS)
+    uk = z.keys(rng, SAMPLE_OPS)
+    uv = w.normal_values(rng, SAMPLE_OPS, DIM)
+    t0 = time.perf_counter()
+    for t in tabs:
+        t.find(fk)
+        t.insert_or_assign(uk, uv)
+    return time.perf_counter() - t0, 2 * SAMPLE_OPS * len(tabs)
+
+
+ORACLE_SAMPLE = (f"oracle (single-threaded C) on 4 dual-bucket LFU tables of 2^20 slots "
+                 f"(1/64 scale) at lambda 0.50/0.75/0.90/1.00, per step one find and one "
+                 f"insert_or_assign of {SAMPLE_OPS} Zipf(1.05) keys each; fill time excluded")
+
+
+def cpu_baseline(steps=24):
+    from paper_2603_17168_gb300 import workloads as w
+    tabs, rng = oracle_tables(w.seed_for(2, 99))
+    z = w.Zipf(ALPHA, UNIVERSE)
+    oracle_step(tabs, rng, z)
+    secs = units = 0
+    for _ in range(steps):
+        s, u = oracle_step(tabs, rng, z)
+        secs += s
+        units += u
+    return {"value": round(units / secs / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": ORACLE_SAMPLE + f", {steps} timed steps ({secs:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    from paper_2603_17168_gb300 import workloads as w
+    tabs, rng = oracle_tables(w.seed_for(2, 99))
+    z = w.Zipf(ALPHA, UNIVERSE)
+    for _ in range(args.warmup):
+        oracle_step(tabs, rng, z)
+    secs = units = 0
+    for _ in range(args.steps):
+        s, u = oracle_step(tabs, rng, z)
+        secs += s
+        units += u
+    value = units / secs / 1e9
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(secs * 1e3 / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (oracle sample, see cpu_baseline)"},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1,
+                             "kind": "oracle", "sample": ORACLE_SAMPLE},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        res = run_reference(args)
+    else:
+        import __graft_entry__ as g
+        g.build()
+        res = run_ours(args)
+        rank, world, _ = dist_env()
+        if res is not None and rank == 0:
+            res["cpu_baseline"] = None if (args.no_cpu_baseline or world > 1) else cpu_baseline()
+    if res is not None:
+        print(json.dumps(res), flush=True)
+    rank, world, _ = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

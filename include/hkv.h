@@ -181,18 +181,27 @@ hkv_status hkv_set_epoch(hkv_table_t t, uint64_t epoch);
 /* Wait for `stream` and return (and clear) the table's latched device error. */
 hkv_status hkv_sync(hkv_table_t t, hkv_stream_t stream);
 
-/* Outcome counters accumulated on the device by the kernels since the last
- * reset, copied to out[HKV_COUNTER_COUNT] (HOST); synchronises `stream`. */
+/* Outcome and traffic counters accumulated on the device by the kernels
+ * since the last reset, copied to out[HKV_COUNTER_COUNT] (HOST);
+ * synchronises `stream`. The traffic counters (digest lines, full-key reads,
+ * score lines) give the bytes each kernel had to move for its inputs. */
 enum {
   HKV_CNT_FIND_HIT = 0,
   HKV_CNT_FIND_MISS = 1,
-  HKV_CNT_UNIQUE = 2,   /* distinct keys of upsert/assign batches */
+  HKV_CNT_UNIQUE = 2,      /* distinct keys of upsert / assign batches */
   HKV_CNT_UPDATED = 3,
-  HKV_CNT_INSERTED = 4, /* claimed a free slot */
-  HKV_CNT_EVICTED = 5,  /* replaced a minimum entry */
-  HKV_CNT_REJECTED = 6, /* refused by admission */
-  HKV_CNT_RETRIES = 7,  /* slot-claim retries after a lost race */
-  HKV_COUNTER_COUNT = 8
+  HKV_CNT_INSERTED = 4,    /* claimed a free slot */
+  HKV_CNT_EVICTED = 5,     /* replaced a minimum entry */
+  HKV_CNT_REJECTED = 6,    /* refused by admission */
+  HKV_CNT_RETRIES = 7,     /* slot-claim retries after a lost race */
+  HKV_CNT_FIND_LINES = 8,  /* 128-B digest lines read by find / contains */
+  HKV_CNT_FIND_KEYS = 9,   /* full keys read by find / contains */
+  HKV_CNT_UPD_LINES = 10,  /* digest lines read by the update phase */
+  HKV_CNT_UPD_KEYS = 11,   /* full keys read by the update phase */
+  HKV_CNT_INS_LINES = 12,  /* digest lines read by the insert phase */
+  HKV_CNT_INS_SCORES = 13, /* 1-KiB score lines read by victim searches */
+  HKV_CNT_INS_KEYS = 14,   /* keys read by victim searches (tie-break) */
+  HKV_COUNTER_COUNT = 15
 };
 hkv_status hkv_read_counters(hkv_table_t t, uint64_t *out, hkv_stream_t stream);
 hkv_status hkv_reset_counters(hkv_table_t t, hkv_stream_t stream);
@@ -202,6 +211,27 @@ hkv_status hkv_reset_counters(hkv_table_t t, hkv_stream_t stream);
  * 0 keeps the current choice. The autotuner in the Python package sets
  * these; defaults follow the value width. */
 hkv_status hkv_set_launch(hkv_table_t t, int find_threads_per_key, int update_threads_per_key);
+
+/* Measurement hook. While enabled, every kernel the library launches for
+ * this table is bracketed by two CUDA events recorded on the launching
+ * stream. hkv_profile_read waits for those events and returns, per kernel
+ * kind (HKV_K_*), the summed device time in ms (ms_out[HKV_KERNEL_KINDS])
+ * and the number of launches (launches_out[HKV_KERNEL_KINDS]), both HOST
+ * arrays, then forgets the records. */
+enum {
+  HKV_K_FIND = 0,
+  HKV_K_DEDUP = 1,
+  HKV_K_UPDATE = 2,
+  HKV_K_INSERT = 3,
+  HKV_K_RECONCILE = 4,
+  HKV_K_STATUS = 5,
+  HKV_K_ERASE = 6,
+  HKV_K_EXPORT = 7,
+  HKV_K_SIZE = 8,
+  HKV_KERNEL_KINDS = 9
+};
+hkv_status hkv_profile_enable(hkv_table_t t, int on);
+hkv_status hkv_profile_read(hkv_table_t t, double *ms_out, uint64_t *launches_out);
 
 /* Message of the calling thread's last error ("" if none). */
 const char *hkv_last_error(void);

@@ -18,10 +18,11 @@ LIB_PATH = os.path.join(PKG, "libhkv.so")
 
 LRU, LFU, EPOCH_LRU, EPOCH_LFU, CUSTOM, CUSTOM_TS_FREQ = range(6)
 ST_UPDATED, ST_INSERTED, ST_REJECTED = 1, 2, 3
-(CNT_FIND_HIT, CNT_FIND_MISS, CNT_UNIQUE, CNT_UPDATED, CNT_INSERTED, CNT_EVICTED,
- CNT_REJECTED, CNT_RETRIES) = range(8)
 COUNTER_NAMES = ("find_hit", "find_miss", "unique", "updated", "inserted", "evicted",
-                 "rejected", "retries")
+                 "rejected", "retries", "find_lines", "find_keys", "upd_lines", "upd_keys",
+                 "ins_lines", "ins_score_lines", "ins_keys")
+KERNEL_NAMES = ("find", "dedup", "update", "insert", "reconcile", "status", "erase", "export",
+                "size")
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "RESERVED_KEY", 3: "DUPLICATE_KEY", 4: "OOM",
                 5: "CUDA", 6: "TIMEOUT", 7: "BUSY"}
 SLOTS = 128
@@ -57,6 +58,8 @@ SIGNATURES = {
     "hkv_read_counters": (_i32, [_vp, _P64, _vp]),
     "hkv_reset_counters": (_i32, [_vp, _vp]),
     "hkv_set_launch": (_i32, [_vp, _i32, _i32]),
+    "hkv_profile_enable": (_i32, [_vp, _i32]),
+    "hkv_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), _P64]),
     "hkv_last_error": (ctypes.c_char_p, []),
 }
 
@@ -248,12 +251,22 @@ class Table:
         _check(load_library().hkv_sync(self._h, _stream(stream)))
 
     def read_counters(self, stream=None) -> dict:
-        arr = (ctypes.c_uint64 * 8)()
+        arr = (ctypes.c_uint64 * len(COUNTER_NAMES))()
         _check(load_library().hkv_read_counters(self._h, arr, _stream(stream)))
         return dict(zip(COUNTER_NAMES, list(arr)))
 
     def reset_counters(self, stream=None):
         _check(load_library().hkv_reset_counters(self._h, _stream(stream)))
+
+    def profile_enable(self, on: bool = True):
+        _check(load_library().hkv_profile_enable(self._h, int(on)))
+
+    def profile_read(self) -> dict:
+        """{kernel: (total ms, launches)} since the last read."""
+        ms = (ctypes.c_double * len(KERNEL_NAMES))()
+        cnt = (ctypes.c_uint64 * len(KERNEL_NAMES))()
+        _check(load_library().hkv_profile_read(self._h, ms, cnt))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_NAMES) if cnt[i]}
 
     def set_launch(self, find_threads_per_key: int = 0, update_threads_per_key: int = 0):
         _check(load_library().hkv_set_launch(self._h, find_threads_per_key,

@@ -149,11 +149,12 @@ __device__ __forceinline__ void load_line(const uint8_t* line, int lane_g, uint3
 // lane compares its 128/G digests and confirms matches against the full
 // key. Every lane of the warp must call this (it ends with a warp ballot).
 // Returns the slot (0..127) of the key in the bucket, or -1; identical on
-// all lanes of a group.
+// all lanes of a group. Adds the full-key loads this lane made to key_reads.
 template <int G, bool CG>
 __device__ __forceinline__ int probe_bucket(const TableDev& t, uint64_t b, uint64_t key,
                                             uint32_t pat4, bool active, int lane_g,
-                                            unsigned group_bits, int group_base) {
+                                            unsigned group_bits, int group_base,
+                                            unsigned& key_reads) {
   int my = -1;
   if (active) {
     uint32_t w[32 / G];
@@ -166,6 +167,7 @@ __device__ __forceinline__ int probe_bucket(const TableDev& t, uint64_t b, uint6
         int bit = __ffs(m) - 1;
         int slot = lane_g * (128 / G) + q * 4 + (bit >> 3);
         uint64_t k = CG ? __ldcg(kb + slot) : __ldg(kb + slot);
+        key_reads++;
         if (k == key) my = slot;
         m &= ~(0xFFu << (bit & ~7));
       }

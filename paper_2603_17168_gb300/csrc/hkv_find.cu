@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kFindThreads)
   const unsigned group_bits = G == 32 ? 0xFFFFFFFFu : (((1u << G) - 1u) << group_base);
   const uint64_t warp = (blockIdx.x * (uint64_t)kFindThreads + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * kFindThreads) >> 5;
-  unsigned hits = 0, misses = 0;
+  unsigned hits = 0, misses = 0, lines = 0, kreads = 0;
 
   for (uint64_t base = warp * KPW; base < n; base += nwarps * KPW) {
     const uint64_t i = base + (lane / G);
@@ -37,12 +37,16 @@ __global__ void __launch_bounds__(kFindThreads)
     uint64_t h = fmix64(key);
     uint64_t b = h & t.bucket_mask;
     uint32_t pat4 = digest_from_hash(h) * 0x01010101u;
-    int slot = probe_bucket<G, false>(t, b, key, pat4, active, lane_g, group_bits, group_base);
+    int slot = probe_bucket<G, false>(t, b, key, pat4, active, lane_g, group_bits, group_base,
+                                      kreads);
+    lines += active && lane_g == 0;
     if (t.dual) {
       uint64_t b2 = second_bucket(t, key);
       bool need = active && slot < 0 && b2 != b;
+      lines += need && lane_g == 0;
       if (__any_sync(0xFFFFFFFFu, need)) {
-        int s2 = probe_bucket<G, false>(t, b2, key, pat4, need, lane_g, group_bits, group_base);
+        int s2 = probe_bucket<G, false>(t, b2, key, pat4, need, lane_g, group_bits, group_base,
+                                        kreads);
         if (need && s2 >= 0) {
           slot = s2;
           b = b2;
@@ -63,9 +67,13 @@ __global__ void __launch_bounds__(kFindThreads)
   }
   hits = __reduce_add_sync(0xFFFFFFFFu, hits);
   misses = __reduce_add_sync(0xFFFFFFFFu, misses);
+  lines = __reduce_add_sync(0xFFFFFFFFu, lines);
+  kreads = __reduce_add_sync(0xFFFFFFFFu, kreads);
   if (lane == 0) {
     count_add(t, HKV_CNT_FIND_HIT, hits);
     count_add(t, HKV_CNT_FIND_MISS, misses);
+    count_add(t, HKV_CNT_FIND_LINES, lines);
+    count_add(t, HKV_CNT_FIND_KEYS, kreads);
   }
 }
 
@@ -93,6 +101,7 @@ void launch_g(const hkv_table_s* t, uint64_t n, const uint64_t* keys, float* out
 hkv_status launch_find(hkv_table_s* t, uint64_t n, const uint64_t* keys, float* values_out,
                        uint8_t* found, uint64_t* scores_out, cudaStream_t s) {
   if (n == 0) return HKV_OK;
+  KernelTimer timer(t->prof, HKV_K_FIND, s);
   bool vec16 = (t->dev.dim % 4 == 0) && ((reinterpret_cast<uintptr_t>(values_out) & 15) == 0);
   switch (t->launch.find_tpk) {
     case 1: launch_g<1>(t, n, keys, values_out, found, scores_out, vec16, s); break;

@@ -38,6 +38,59 @@ struct CudaEvents {
   }
 };
 
+// Per-table kernel timer (hkv_profile_*): event pairs on the launching stream.
+struct Profiler {
+  bool on = false;
+  std::mutex mu;
+  std::vector<cudaEvent_t> pool;
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  cudaEvent_t get() {
+    cudaEvent_t e;
+    if (pool.empty()) {
+      cudaEventCreate(&e);
+    } else {
+      e = pool.back();
+      pool.pop_back();
+    }
+    return e;
+  }
+  ~Profiler() {
+    for (auto& r : recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+// Brackets one kernel launch with profiling events when profiling is on.
+class KernelTimer {
+ public:
+  KernelTimer(Profiler& p, int kind, cudaStream_t s) : p_(p), kind_(kind), s_(s) {
+    if (!p_.on) return;
+    std::lock_guard<std::mutex> lk(p_.mu);
+    a_ = p_.get();
+    cudaEventRecord(a_, s_);
+  }
+  ~KernelTimer() {
+    if (!a_) return;
+    std::lock_guard<std::mutex> lk(p_.mu);
+    cudaEvent_t b = p_.get();
+    cudaEventRecord(b, s_);
+    p_.recs.push_back({kind_, a_, b});
+  }
+
+ private:
+  Profiler& p_;
+  int kind_;
+  cudaStream_t s_;
+  cudaEvent_t a_ = nullptr;
+};
+
 // Launch shape chosen for the probe kernels.
 struct LaunchCfg {
   int find_tpk = 8;    // threads per key, find / contains
@@ -64,6 +117,7 @@ struct hkv_table_s {
   float** slices_dev = nullptr;
   cudaMemPool_t pool = nullptr;         // stream-ordered scratch allocations
   hkv::TripleGroup<hkv::CudaEvents> sched;
+  hkv::Profiler prof;
 };
 
 namespace hkv {

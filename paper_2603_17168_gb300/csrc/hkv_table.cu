@@ -101,6 +101,7 @@ hkv_status launch_size(hkv_table_s* t, unsigned long long* out_dev, cudaStream_t
   cudaMemsetAsync(out_dev, 0, 8, s);
   const uint64_t n16 = t->num_buckets * kSlots / 16;
   uint64_t blocks = std::min<uint64_t>((n16 + 255) / 256, (uint64_t)t->num_sms * 8);
+  KernelTimer timer(t->prof, HKV_K_SIZE, s);
   size_kernel<<<(unsigned)std::max<uint64_t>(blocks, 1), 256, 0, s>>>(t->dev.digests, n16, out_dev);
   return cuda_status(cudaGetLastError(), "size launch");
 }
@@ -111,6 +112,7 @@ hkv_status launch_export(hkv_table_s* t, uint64_t offset, uint64_t n_slots, uint
   cudaMemsetAsync(count_out, 0, 8, s);
   if (n_slots == 0) return cuda_status(cudaGetLastError(), "export");
   uint64_t blocks = std::min<uint64_t>((n_slots + 255) / 256, (uint64_t)t->num_sms * 8);
+  KernelTimer timer(t->prof, HKV_K_EXPORT, s);
   export_kernel<<<(unsigned)std::max<uint64_t>(blocks, 1), 256, 0, s>>>(
       t->dev, offset, n_slots, reinterpret_cast<unsigned long long*>(count_out), keys, values,
       scores, slots);
@@ -357,7 +359,7 @@ hkv_status hkv_erase(hkv_table_t t, uint64_t n, const uint64_t* keys, hkv_stream
 hkv_status hkv_size(hkv_table_t t, uint64_t* out, hkv_stream_t stream) {
   if (bad(t) || !out) return fail(HKV_ERR_INVALID_ARG, "size arguments");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  unsigned long long* d = t->dev.counters + 16;  // spare words after the counters
+  unsigned long long* d = t->dev.counters + 24;  // spare words after the counters
   {
     auto lk = t->sched.acquire(kReader, s);
     hkv_status rc = launch_size(t, d, s);
@@ -418,6 +420,35 @@ hkv_status hkv_reset_counters(hkv_table_t t, hkv_stream_t stream) {
   return cuda_status(cudaMemsetAsync(t->dev.counters, 0, HKV_COUNTER_COUNT * 8,
                                      static_cast<cudaStream_t>(stream)),
                      "reset counters");
+}
+
+hkv_status hkv_profile_enable(hkv_table_t t, int on) {
+  if (bad(t)) return fail(HKV_ERR_INVALID_ARG, "null table");
+  std::lock_guard<std::mutex> lk(t->prof.mu);
+  t->prof.on = on != 0;
+  return HKV_OK;
+}
+
+hkv_status hkv_profile_read(hkv_table_t t, double* ms_out, uint64_t* launches_out) {
+  if (bad(t) || !ms_out || !launches_out) return fail(HKV_ERR_INVALID_ARG, "profile arguments");
+  std::lock_guard<std::mutex> lk(t->prof.mu);
+  for (int k = 0; k < HKV_KERNEL_KINDS; ++k) {
+    ms_out[k] = 0;
+    launches_out[k] = 0;
+  }
+  hkv_status rc = HKV_OK;
+  for (auto& r : t->prof.recs) {
+    cudaError_t e = cudaEventSynchronize(r.b);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess && rc == HKV_OK) rc = cuda_status(e, "profile events");
+    ms_out[r.kind] += ms;
+    launches_out[r.kind] += 1;
+    t->prof.pool.push_back(r.a);
+    t->prof.pool.push_back(r.b);
+  }
+  t->prof.recs.clear();
+  return rc;
 }
 
 hkv_status hkv_set_launch(hkv_table_t t, int find_tpk, int update_tpk) {

@@ -94,7 +94,7 @@ constexpr int kDedupSmem = (1 << kDedupSmemBits) * (int)sizeof(DedupEntry);
 
 __global__ void __launch_bounds__(kDedupThreads)
     dedup_kernel(uint64_t n, const uint64_t* __restrict__ keys, Scratch s, uint32_t* err,
-                 int deterministic, unsigned long long* uniq_counter) {
+                 int deterministic, unsigned long long* uniq_counter, TableDev tcount) {
   extern __shared__ DedupEntry sm[];
   constexpr uint32_t kMask = (1u << kDedupSmemBits) - 1;
   for (int p = threadIdx.x; p < (1 << kDedupSmemBits); p += kDedupThreads) {
@@ -146,6 +146,8 @@ __global__ void __launch_bounds__(kDedupThreads)
     }
     unsigned long long u = warp_append(uniq_counter, first);
     if (first) s.ulist[u] = (uint32_t)gp;
+    const unsigned nfirst = __popc(__ballot_sync(kFull, first));
+    if ((threadIdx.x & 31) == 0) count_add(tcount, HKV_CNT_UNIQUE, nfirst);
     if (have) sm[p].cnt_m1 = (uint32_t)gp;  // reuse: global entry of this key
   }
   __syncthreads();
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(kUpdThreads)
   const uint64_t warp = (blockIdx.x * (uint64_t)kUpdThreads + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * kUpdThreads) >> 5;
   const uint64_t nu = s.cnt[kCntUnique];
-  unsigned updated = 0;
+  unsigned updated = 0, lines = 0, kreads = 0;
 
   for (uint64_t base = warp * KPW; base < nu; base += nwarps * KPW) {
     const uint64_t u = base + (lane / G);
@@ -184,12 +186,16 @@ __global__ void __launch_bounds__(kUpdThreads)
     uint64_t h = fmix64(key);
     uint64_t b = h & t.bucket_mask;
     uint32_t pat4 = digest_from_hash(h) * 0x01010101u;
-    int slot = probe_bucket<G, false>(t, b, key, pat4, active, lane_g, group_bits, group_base);
+    int slot = probe_bucket<G, false>(t, b, key, pat4, active, lane_g, group_bits, group_base,
+                                      kreads);
+    lines += active && lane_g == 0;
     if (t.dual) {
       uint64_t b2 = second_bucket(t, key);
       bool need = active && slot < 0 && b2 != b;
+      lines += need && lane_g == 0;
       if (__any_sync(kFull, need)) {
-        int s2 = probe_bucket<G, false>(t, b2, key, pat4, need, lane_g, group_bits, group_base);
+        int s2 = probe_bucket<G, false>(t, b2, key, pat4, need, lane_g, group_bits, group_base,
+                                        kreads);
         if (need && s2 >= 0) {
           slot = s2;
           b = b2;
@@ -217,7 +223,13 @@ __global__ void __launch_bounds__(kUpdThreads)
     }
   }
   updated = __reduce_add_sync(kFull, updated);
-  if (lane == 0) count_add(t, HKV_CNT_UPDATED, updated);
+  lines = __reduce_add_sync(kFull, lines);
+  kreads = __reduce_add_sync(kFull, kreads);
+  if (lane == 0) {
+    count_add(t, HKV_CNT_UPDATED, updated);
+    count_add(t, HKV_CNT_UPD_LINES, lines);
+    count_add(t, HKV_CNT_UPD_KEYS, kreads);
+  }
 }
 
 // --------------------------------------------------------- phase I insert
@@ -260,7 +272,8 @@ __device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_
 // (score, key) order or is being rewritten. All lanes take part.
 __device__ __forceinline__ bool victim_is_min(const TableDev& t, uint64_t b1, uint64_t b2, bool two,
                                               uint64_t g, unsigned long long smin,
-                                              unsigned long long kmin, int lane) {
+                                              unsigned long long kmin, int lane,
+                                              unsigned& kreads) {
   bool bad = false;
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
@@ -279,6 +292,7 @@ __device__ __forceinline__ bool victim_is_min(const TableDev& t, uint64_t b1, ui
       if (sv[q] < smin) { bad = true; continue; }
       if (sv[q] == smin) {
         const uint64_t kx = __ldcg(t.keys + x);
+        kreads++;
         bad |= kx == kLockedKey || kx < kmin;
       }
     }
@@ -296,6 +310,7 @@ __global__ void __launch_bounds__(kInsThreads)
   const uint64_t nwarps = ((uint64_t)gridDim.x * kInsThreads) >> 5;
   const uint64_t nm = s.cnt[kCntMiss];
   unsigned inserted = 0, evicted = 0, rejected = 0, retries = 0;
+  unsigned lines = 0, score_lines = 0, kreads = 0;
 
   for (uint64_t j = warp; j < nm; j += nwarps) {
     const uint32_t e = s.mlist[j];
@@ -315,6 +330,7 @@ __global__ void __launch_bounds__(kInsThreads)
     for (; attempt < kMaxClaimAttempts; ++attempt) {
       // back off with per-key jitter so warps colliding on a slot fall apart
       if (attempt) __nanosleep((32u << (attempt < 6 ? attempt : 6)) + ((unsigned)(h >> 17) & 255u));
+      lines += two ? 2 : 1;
       const uint32_t w1 = __ldcg(reinterpret_cast<const uint32_t*>(t.digests + b1 * kSlots) + lane);
       const uint32_t z1 = __vcmpeq4(w1, 0u);
       const int free1 = __reduce_add_sync(kFull, (unsigned)__popc(z1) >> 3);
@@ -353,6 +369,7 @@ __global__ void __launch_bounds__(kInsThreads)
       // Full: minimum (score, key) over the candidate slots (Algorithm 2
       // line 10; Algorithm 3 phase D2 takes both buckets' slots).
       unsigned long long sv[8];
+      score_lines += two ? 2 : 1;
       {
         const ulonglong2* p1 = reinterpret_cast<const ulonglong2*>(t.scores + b1 * kSlots) + lane * 2;
         ulonglong2 a = __ldcg(p1), c = __ldcg(p1 + 1);
@@ -381,6 +398,7 @@ __global__ void __launch_bounds__(kInsThreads)
         if (sv[q] != smin) continue;
         const uint64_t bq = q < 4 ? b1 : b2;
         const uint64_t kq = __ldcg(t.keys + bq * kSlots + lane * 4 + (q & 3));
+        kreads++;
         if (kq >= kLockedKey) { busy = true; continue; }
         if (kq < kbest) { kbest = kq; qbest = q; }
       }
@@ -410,7 +428,8 @@ __global__ void __launch_bounds__(kInsThreads)
       // values only grow while a bucket is full, so a victim that passes
       // here is the minimum from now on: this is the claim's linearisation
       // point.
-      if (!victim_is_min(t, b1, b2, two, g, smin, kmin, lane)) {
+      unsigned vreads = 0;  // validation re-reads hit L2: not counted as method traffic
+      if (!victim_is_min(t, b1, b2, two, g, smin, kmin, lane, vreads)) {
         if (lane == owner) atomicExch(reinterpret_cast<unsigned long long*>(t.keys + g), kmin);
         retries++;
         continue;
@@ -434,11 +453,15 @@ __global__ void __launch_bounds__(kInsThreads)
     if (attempt == kMaxClaimAttempts && lane == 0) latch_error(t.err, HKV_ERR_TIMEOUT);
     if (lane == 0) s.tstatus[e] = outcome;
   }
+  kreads = __reduce_add_sync(kFull, kreads);
   if (lane == 0) {
     count_add(t, HKV_CNT_INSERTED, inserted);
     count_add(t, HKV_CNT_EVICTED, evicted);
     count_add(t, HKV_CNT_REJECTED, rejected);
     count_add(t, HKV_CNT_RETRIES, retries);
+    count_add(t, HKV_CNT_INS_LINES, lines);
+    count_add(t, HKV_CNT_INS_SCORES, score_lines);
+    count_add(t, HKV_CNT_INS_KEYS, kreads);
   }
 }
 
@@ -508,12 +531,15 @@ __global__ void __launch_bounds__(kUpdThreads)
     uint64_t b = h & t.bucket_mask;
     const uint32_t pat4 = digest_from_hash(h) * 0x01010101u;
     // Duplicates in the batch may clear the slot concurrently: read through L2.
-    int slot = probe_bucket<G, true>(t, b, key, pat4, active, lane_g, group_bits, group_base);
+    unsigned kreads = 0;
+    int slot = probe_bucket<G, true>(t, b, key, pat4, active, lane_g, group_bits, group_base,
+                                     kreads);
     if (t.dual) {
       const uint64_t b2 = second_bucket(t, key);
       const bool need = active && slot < 0 && b2 != b;
       if (__any_sync(kFull, need)) {
-        int s2 = probe_bucket<G, true>(t, b2, key, pat4, need, lane_g, group_bits, group_base);
+        int s2 = probe_bucket<G, true>(t, b2, key, pat4, need, lane_g, group_bits, group_base,
+                                       kreads);
         if (need && s2 >= 0) { slot = s2; b = b2; }
       }
     }
@@ -582,6 +608,7 @@ template <int G, bool UPSERT>
 void launch_update_g(hkv_table_s* t, uint64_t n, const Scratch& s, const float* values,
                      const uint64_t* scores, ScoreCtx ctx, bool vec16, cudaStream_t st) {
   const unsigned grid = grid_for(t, n * G, kUpdThreads, 2048 / kUpdThreads);
+  KernelTimer timer(t->prof, HKV_K_UPDATE, st);
   if (vec16)
     update_kernel<G, true, UPSERT><<<grid, kUpdThreads, 0, st>>>(t->dev, s, values, scores, ctx);
   else
@@ -604,8 +631,10 @@ void launch_update(hkv_table_s* t, uint64_t n, const Scratch& s, const float* va
 void launch_dedup(hkv_table_s* t, uint64_t n, const uint64_t* keys, const Scratch& s,
                   cudaStream_t st) {
   const unsigned grid = (unsigned)((n + kDedupTile - 1) / kDedupTile);
+  KernelTimer timer(t->prof, HKV_K_DEDUP, st);
   dedup_kernel<<<grid, kDedupThreads, kDedupSmem, st>>>(n, keys, s, t->dev.err,
-                                                        t->opts.deterministic, s.cnt + kCntUnique);
+                                                        t->opts.deterministic, s.cnt + kCntUnique,
+                                                        t->dev);
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
@@ -636,14 +665,22 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
   launch_dedup(t, n, keys, s, st);
   launch_update<true>(t, n, s, values, scores, ctx, vec16, st);
   const unsigned ig = grid_for(t, n * 32, kInsThreads, 2048 / kInsThreads);
-  if (vec16)
-    insert_kernel<true><<<ig, kInsThreads, 0, st>>>(t->dev, s, values, scores, ctx);
-  else
-    insert_kernel<false><<<ig, kInsThreads, 0, st>>>(t->dev, s, values, scores, ctx);
-  reconcile_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(t->dev, s, ev_keys, ev_scores,
-                                                            ev_values);
-  if (status_out || n_evicted)
+  {
+    KernelTimer timer(t->prof, HKV_K_INSERT, st);
+    if (vec16)
+      insert_kernel<true><<<ig, kInsThreads, 0, st>>>(t->dev, s, values, scores, ctx);
+    else
+      insert_kernel<false><<<ig, kInsThreads, 0, st>>>(t->dev, s, values, scores, ctx);
+  }
+  {
+    KernelTimer timer(t->prof, HKV_K_RECONCILE, st);
+    reconcile_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(t->dev, s, ev_keys, ev_scores,
+                                                              ev_values);
+  }
+  if (status_out || n_evicted) {
+    KernelTimer timer(t->prof, HKV_K_STATUS, st);
     status_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(n, s, status_out, n_evicted);
+  }
   cudaFreeAsync(a.base, st);
   return cuda_status(cudaGetLastError(), "insert_or_assign launch");
 }
@@ -675,6 +712,7 @@ hkv_status launch_erase(hkv_table_s* t, uint64_t n, const uint64_t* keys, cudaSt
   Scratch s{};
   s.cnt = static_cast<unsigned long long*>(base);
   cudaMemsetAsync(s.cnt, 0, kCntWords * 8, st);
+  KernelTimer timer(t->prof, HKV_K_ERASE, st);
   validate_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(n, keys, s, t->dev.err);
   erase_kernel<8><<<grid_for(t, n * 8, kUpdThreads, 2048 / kUpdThreads), kUpdThreads, 0, st>>>(
       t->dev, n, keys, s);

@@ -109,3 +109,51 @@ MULTI_DIMS = (16, 32, 64, 64, 128, 128, 256, 8)
 MULTI_SLOTS = (1 << 25, 1 << 25, 1 << 24, 1 << 24, 1 << 23, 1 << 23, 1 << 22, 1 << 25)
 TIERED = dict(name="tiered", slots=1 << 28, dim=128, hbm_value_bytes=48 << 30, zipf_alpha=0.99,
               universe=1 << 34, batch=1 << 20)
+
+
+# ---------------------------------------------------------------------------
+# Device-side twins of the generators (torch on the GPU), for benchmark
+# inputs too large to draw on the host quickly. Same constructions as above;
+# the streams differ from numpy's, so parity tests use the numpy versions.
+
+def rank_to_key_torch(ranks):
+    import torch
+    g = torch.tensor(int(GOLDEN) - (1 << 64), dtype=torch.int64, device=ranks.device)
+    return (ranks.to(torch.int64) * g) & ((1 << 63) - 1)
+
+
+def uniform_keys_torch(gen, n: int, universe: int, device="cuda"):
+    import torch
+    r = torch.randint(1, universe + 1, (n,), dtype=torch.int64, device=device, generator=gen)
+    return rank_to_key_torch(r)
+
+
+def zipf_ranks_torch(gen, z: Zipf, n: int, device="cuda"):
+    import torch
+    out = torch.empty(n, dtype=torch.int64, device=device)
+    todo = torch.arange(n, device=device)
+    s = z.s
+
+    def H(x):
+        lx = torch.log(x)
+        t = (1.0 - s) * lx
+        return torch.where(t.abs() > 1e-8, torch.expm1(t) / torch.where(t == 0, 1.0, t), 1.0) * lx
+
+    def Hinv(y):
+        t = (1.0 - s) * y
+        return torch.exp(torch.where(t.abs() > 1e-8, torch.log1p(t) / torch.where(t == 0, 1.0, t),
+                                     1.0) * y)
+
+    while todo.numel():
+        u = z.h_n + torch.rand(todo.numel(), dtype=torch.float64, device=device,
+                               generator=gen) * (z.h_x1 - z.h_n)
+        x = Hinv(u)
+        k = torch.clamp(torch.floor(x + 0.5), 1, z.N)
+        ok = (k - x <= z.cut) | (u >= H(k + 0.5) - torch.exp(-s * torch.log(k)))
+        out[todo[ok]] = k[ok].to(torch.int64)
+        todo = todo[~ok]
+    return out
+
+
+def zipf_keys_torch(gen, z: Zipf, n: int, device="cuda"):
+    return rank_to_key_torch(zipf_ranks_torch(gen, z, n, device))
