@@ -117,6 +117,60 @@ __device__ __forceinline__ uint64_t policy_score(int policy, bool hit, uint64_t 
   }
 }
 
+// ------------------------------------------------------ block-level atomics
+//
+// Atomics with a return value on one address serialise in L2; issued per
+// warp they dominated whole kernels. These helpers aggregate a block first
+// and touch the global word once per block. Every thread of the block must
+// call them (they synchronise the block).
+
+// Add per-thread values to NC table counters, one global atomic per counter
+// per block.
+template <int NC>
+__device__ __forceinline__ void flush_counts(const TableDev& t, const int (&which)[NC],
+                                             const unsigned (&vals)[NC]) {
+  __shared__ unsigned long long acc[NC];
+  if (threadIdx.x < NC) acc[threadIdx.x] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const unsigned w = __reduce_add_sync(0xFFFFFFFFu, vals[c]);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(&acc[c], (unsigned long long)w);
+  }
+  __syncthreads();
+  if (threadIdx.x < NC && acc[threadIdx.x]) atomicAdd(t.counters + which[threadIdx.x], acc[threadIdx.x]);
+}
+
+// Reserve `count` consecutive list positions per thread from a global
+// counter; returns this thread's first position.
+__device__ __forceinline__ unsigned long long block_reserve(unsigned long long* counter,
+                                                            unsigned count) {
+  __shared__ unsigned wsum[32];
+  __shared__ unsigned long long base;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  unsigned incl = count;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned tot = 0;
+    for (int w = 0; w < nw; ++w) {
+      const unsigned c = wsum[w];
+      wsum[w] = tot;
+      tot += c;
+    }
+    base = tot ? atomicAdd(counter, (unsigned long long)tot) : 0ull;
+  }
+  __syncthreads();
+  const unsigned long long pos = base + wsum[wid] + (incl - count);
+  __syncthreads();
+  return pos;
+}
+
 // Byte mask of slots whose digest byte equals the pattern: SIMD compare of
 // four digests per 32-bit word (Algorithm 1's __vcmpeq4 step).
 __device__ __forceinline__ uint32_t match4(uint32_t word, uint32_t pat4) {

@@ -65,16 +65,9 @@ __global__ void __launch_bounds__(kFindThreads)
       misses += !hit;
     }
   }
-  hits = __reduce_add_sync(0xFFFFFFFFu, hits);
-  misses = __reduce_add_sync(0xFFFFFFFFu, misses);
-  lines = __reduce_add_sync(0xFFFFFFFFu, lines);
-  kreads = __reduce_add_sync(0xFFFFFFFFu, kreads);
-  if (lane == 0) {
-    count_add(t, HKV_CNT_FIND_HIT, hits);
-    count_add(t, HKV_CNT_FIND_MISS, misses);
-    count_add(t, HKV_CNT_FIND_LINES, lines);
-    count_add(t, HKV_CNT_FIND_KEYS, kreads);
-  }
+  const int which[4] = {HKV_CNT_FIND_HIT, HKV_CNT_FIND_MISS, HKV_CNT_FIND_LINES, HKV_CNT_FIND_KEYS};
+  const unsigned vals[4] = {hits, misses, lines, kreads};
+  flush_counts(t, which, vals);
 }
 
 template <int G>

@@ -5,28 +5,32 @@
 //   dedup     collapse duplicate keys (last occurrence's value, multiplicity
 //             m): per-block shared-memory hash aggregation, then a global
 //             open-addressing table, so a Zipf-hot key costs one global
-//             atomic per block instead of one per occurrence;
+//             atomic per block instead of one per occurrence. The distinct
+//             keys get dense indices u (one list reservation per block);
 //   update    phase U: probe every distinct key (G lanes per key, digest
-//             line + key confirm) and update residents in place; misses are
-//             appended to a compact list;
-//   insert    phase I: one warp per new key claims a free slot with a CAS
-//             on the key word (EMPTY -> LOCKED), or, when the bucket (both
-//             buckets in dual mode) is full, reduces the minimum (score, key)
-//             over the 128 (256) slots, applies admission control, CAS-locks
-//             the victim, re-validates its score under the lock and replaces
-//             it (Algorithm 2 lines 6-14, Algorithm 3);
+//             line + key confirm) and update residents in place; a miss
+//             leaves (key, source row, multiplicity) at its index u;
+//   insert    phase I: a warp takes 32 consecutive u, and for each miss
+//             claims a free slot with a CAS on the key word (EMPTY ->
+//             LOCKED), or, when the bucket (both buckets in dual mode) is
+//             full, reduces the minimum (score, key) over the 128 (256)
+//             slots, applies admission control, CAS-locks the victim and
+//             replaces it (Algorithm 2 lines 6-14, Algorithm 3);
 //   reconcile a victim that was itself inserted by this batch is not an
 //             eviction: its key becomes REJECTED and it is dropped from the
-//             evicted output;
+//             evicted output, which is compacted here;
 //   status    broadcast each distinct key's status to all its occurrences.
 // Phase U finishing before phase I starts is what makes the paper's claim
 // "no update races an eviction" hold for real batches.
 //
-// Single-bucket claims are linearisable (a slot's (score, key) only grows
-// while a bucket is full, and a victim is re-validated under its lock), and
-// any serial order of "insert if free, else replace the minimum iff larger"
-// ends with each bucket holding the largest 128 (score, key) pairs; so the
-// single-bucket result does not depend on the schedule.
+// Single-bucket claims are linearisable: while a bucket is full a slot's
+// (score, key) only grows; a victim search that meets a locked slot among
+// the minimum-score candidates re-reads instead of choosing around it; and
+// the victim's score is re-checked under its lock, which catches a score
+// and key read from two different occupants. Any serial order of "insert if
+// free, else replace the minimum iff larger" ends with each bucket holding
+// the largest 128 (score, key) pairs, so the single-bucket result does not
+// depend on the schedule.
 #include "hkv_internal.h"
 
 namespace hkv {
@@ -41,7 +45,7 @@ struct DedupEntry {
 };
 static_assert(sizeof(DedupEntry) == 16, "dedup entry layout");
 
-enum : int { kCntUnique = 0, kCntMiss = 1, kCntEvRaw = 2, kCntEvOut = 3, kAbort = 4, kCntWords = 8 };
+enum : int { kCntUnique = 0, kCntEvOut = 1, kAbort = 2, kCntWords = 8 };
 
 struct Scratch {
   DedupEntry* tab;
@@ -49,12 +53,15 @@ struct Scratch {
   int tab_bits;
   uint8_t* tstatus;          // [T] status per dedup entry
   uint32_t* slot_of;         // [n] dedup entry of each batch position
-  uint32_t* ulist;           // [n] dedup entries of distinct keys
-  uint32_t* mlist;           // [n] dedup entries of keys that missed in phase U
+  uint32_t* ulist;           // [n] dedup entry of distinct key u
+  uint8_t* mflag;            // [n] 1 if distinct key u missed in phase U
+  uint64_t* mkey;            // [n] key u (misses)
+  uint32_t* mi;              // [n] batch index of its last occurrence (misses)
+  uint32_t* mm;              // [n] its multiplicity (misses)
   unsigned long long* cnt;   // [kCntWords]
-  uint64_t* evk;             // [n] raw victims
-  uint64_t* evs;             // [n]
-  float* evv;                // [n][dim] or null
+  uint64_t* evk;             // [n] victim of distinct key u, kEmptyKey if none
+  uint64_t* evs;             // [n] its score
+  float* evv;                // [n][dim] its value, or null
 };
 
 __device__ __forceinline__ uint64_t dedup_pos(uint64_t key, int bits) {
@@ -71,33 +78,22 @@ __device__ __forceinline__ void abort_batch(const Scratch& s, uint32_t* err, uin
   atomicExch(s.cnt + kAbort, 1ull);
 }
 
-// Warp-aggregated append of `want` lanes to a list; returns each lane's slot.
-__device__ __forceinline__ unsigned long long warp_append(unsigned long long* counter, bool want) {
-  unsigned bal = __ballot_sync(kFull, want);
-  unsigned long long base = 0;
-  int lane = threadIdx.x & 31;
-  if (bal) {
-    int leader = __ffs(bal) - 1;
-    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(bal));
-    base = __shfl_sync(kFull, base, leader);
-  }
-  return base + __popc(bal & ((1u << lane) - 1u));
-}
-
 // ------------------------------------------------------------------- dedup
 
-constexpr int kDedupThreads = 512;
+constexpr int kDedupThreads = 256;
 constexpr int kDedupKPT = 4;
-constexpr int kDedupTile = kDedupThreads * kDedupKPT;
-constexpr int kDedupSmemBits = 12;  // 4096 entries for a tile of 2048 keys
-constexpr int kDedupSmem = (1 << kDedupSmemBits) * (int)sizeof(DedupEntry);
+constexpr int kDedupTile = kDedupThreads * kDedupKPT;           // 1024 keys
+constexpr int kDedupSmemBits = 11;                              // 2048 entries
+constexpr int kDedupEntries = 1 << kDedupSmemBits;
+constexpr int kDedupPerThread = kDedupEntries / kDedupThreads;  // 8
+constexpr int kDedupSmem = kDedupEntries * (int)sizeof(DedupEntry);
 
 __global__ void __launch_bounds__(kDedupThreads)
-    dedup_kernel(uint64_t n, const uint64_t* __restrict__ keys, Scratch s, uint32_t* err,
-                 int deterministic, unsigned long long* uniq_counter, TableDev tcount) {
+    dedup_kernel(uint64_t n, const uint64_t* __restrict__ keys, Scratch s, TableDev t,
+                 int deterministic) {
   extern __shared__ DedupEntry sm[];
-  constexpr uint32_t kMask = (1u << kDedupSmemBits) - 1;
-  for (int p = threadIdx.x; p < (1 << kDedupSmemBits); p += kDedupThreads) {
+  constexpr uint32_t kMask = kDedupEntries - 1;
+  for (int p = threadIdx.x; p < kDedupEntries; p += kDedupThreads) {
     sm[p].key = kEmptyKey;
     sm[p].nlast = 0xFFFFFFFFu;
     sm[p].cnt_m1 = 0xFFFFFFFFu;
@@ -108,16 +104,16 @@ __global__ void __launch_bounds__(kDedupThreads)
 #pragma unroll
   for (int j = 0; j < kDedupKPT; ++j) {
     pos[j] = -1;
-    uint64_t idx = tile0 + (uint64_t)j * kDedupThreads + threadIdx.x;
+    const uint64_t idx = tile0 + (uint64_t)j * kDedupThreads + threadIdx.x;
     if (idx >= n) continue;
-    uint64_t k = __ldg(keys + idx);
+    const uint64_t k = __ldg(keys + idx);
     if (k >= kFirstReserved) {
-      abort_batch(s, err, HKV_ERR_RESERVED_KEY);
+      abort_batch(s, t.err, HKV_ERR_RESERVED_KEY);
       continue;
     }
     uint32_t p = (uint32_t)dedup_pos(k, kDedupSmemBits);
-    for (;;) {  // at most 2048 distinct keys in 4096 entries: terminates
-      unsigned long long old = atomicCAS(&sm[p].key, kEmptyKey, (unsigned long long)k);
+    for (;;) {  // at most 1024 distinct keys in 2048 entries: terminates
+      const unsigned long long old = atomicCAS(&sm[p].key, kEmptyKey, (unsigned long long)k);
       if (old == kEmptyKey || old == k) break;
       p = (p + 1) & kMask;
     }
@@ -126,37 +122,49 @@ __global__ void __launch_bounds__(kDedupThreads)
     pos[j] = (int)p;
   }
   __syncthreads();
-  for (int p = threadIdx.x; p < (1 << kDedupSmemBits); p += kDedupThreads) {
-    unsigned long long k = sm[p].key;
-    bool have = k != kEmptyKey;
+  // Merge this tile's distinct keys into the global table.
+  uint32_t gps[kDedupPerThread];
+  unsigned nfirst = 0, firsts = 0;
+#pragma unroll
+  for (int q = 0; q < kDedupPerThread; ++q) {
+    const int p = threadIdx.x + q * kDedupThreads;
+    gps[q] = 0;
+    const unsigned long long k = sm[p].key;
+    if (k == kEmptyKey) continue;
+    const uint32_t c = sm[p].cnt_m1 + 1u;
+    uint64_t gp = dedup_pos(k, s.tab_bits);
     bool first = false;
-    uint64_t gp = 0;
-    if (have) {
-      uint32_t c = sm[p].cnt_m1 + 1u;
-      gp = dedup_pos(k, s.tab_bits);
-      for (;;) {  // table holds >= 2n entries: terminates
-        unsigned long long old = atomicCAS(&s.tab[gp].key, kEmptyKey, k);
-        if (old == kEmptyKey) { first = true; break; }
-        if (old == k) break;
-        gp = (gp + 1) & s.tab_mask;
-      }
-      atomicMin(&s.tab[gp].nlast, sm[p].nlast);
-      atomicAdd(&s.tab[gp].cnt_m1, c);
-      if (deterministic && (!first || c > 1)) abort_batch(s, err, HKV_ERR_DUPLICATE_KEY);
+    for (;;) {  // the table holds >= 2n entries: terminates
+      const unsigned long long old = atomicCAS(&s.tab[gp].key, kEmptyKey, k);
+      if (old == kEmptyKey) { first = true; break; }
+      if (old == k) break;
+      gp = (gp + 1) & s.tab_mask;
     }
-    unsigned long long u = warp_append(uniq_counter, first);
-    if (first) s.ulist[u] = (uint32_t)gp;
-    const unsigned nfirst = __popc(__ballot_sync(kFull, first));
-    if ((threadIdx.x & 31) == 0) count_add(tcount, HKV_CNT_UNIQUE, nfirst);
-    if (have) sm[p].cnt_m1 = (uint32_t)gp;  // reuse: global entry of this key
+    atomicMin(&s.tab[gp].nlast, sm[p].nlast);
+    atomicAdd(&s.tab[gp].cnt_m1, c);
+    if (deterministic && (!first || c > 1)) abort_batch(s, t.err, HKV_ERR_DUPLICATE_KEY);
+    gps[q] = (uint32_t)gp;
+    sm[p].cnt_m1 = (uint32_t)gp;  // reuse: global entry of this key
+    if (first) {
+      firsts |= 1u << q;
+      nfirst++;
+    }
   }
-  __syncthreads();
+  // One list reservation per block for the keys this block saw first
+  // (block_reserve also synchronises the block: the smem entries are final).
+  unsigned long long u = block_reserve(s.cnt + kCntUnique, nfirst);
+#pragma unroll
+  for (int q = 0; q < kDedupPerThread; ++q)
+    if (firsts & (1u << q)) s.ulist[u++] = gps[q];
 #pragma unroll
   for (int j = 0; j < kDedupKPT; ++j) {
     if (pos[j] < 0) continue;
-    uint64_t idx = tile0 + (uint64_t)j * kDedupThreads + threadIdx.x;
+    const uint64_t idx = tile0 + (uint64_t)j * kDedupThreads + threadIdx.x;
     s.slot_of[idx] = sm[pos[j]].cnt_m1;
   }
+  const int which[1] = {HKV_CNT_UNIQUE};
+  const unsigned vals[1] = {nfirst};
+  flush_counts(t, which, vals);
 }
 
 // ----------------------------------------------------------- phase U probe
@@ -181,21 +189,21 @@ __global__ void __launch_bounds__(kUpdThreads)
   for (uint64_t base = warp * KPW; base < nu; base += nwarps * KPW) {
     const uint64_t u = base + (lane / G);
     const bool active = u < nu;
-    uint32_t e = active ? s.ulist[u] : 0;
-    uint64_t key = active ? s.tab[e].key : kEmptyKey;
-    uint64_t h = fmix64(key);
+    const uint32_t e = active ? s.ulist[u] : 0;
+    const uint64_t key = active ? s.tab[e].key : kEmptyKey;
+    const uint64_t h = fmix64(key);
     uint64_t b = h & t.bucket_mask;
-    uint32_t pat4 = digest_from_hash(h) * 0x01010101u;
+    const uint32_t pat4 = digest_from_hash(h) * 0x01010101u;
     int slot = probe_bucket<G, false>(t, b, key, pat4, active, lane_g, group_bits, group_base,
                                       kreads);
     lines += active && lane_g == 0;
     if (t.dual) {
-      uint64_t b2 = second_bucket(t, key);
-      bool need = active && slot < 0 && b2 != b;
+      const uint64_t b2 = second_bucket(t, key);
+      const bool need = active && slot < 0 && b2 != b;
       lines += need && lane_g == 0;
       if (__any_sync(kFull, need)) {
-        int s2 = probe_bucket<G, false>(t, b2, key, pat4, need, lane_g, group_bits, group_base,
-                                        kreads);
+        const int s2 = probe_bucket<G, false>(t, b2, key, pat4, need, lane_g, group_bits,
+                                              group_base, kreads);
         if (need && s2 >= 0) {
           slot = s2;
           b = b2;
@@ -203,33 +211,33 @@ __global__ void __launch_bounds__(kUpdThreads)
       }
     }
     const bool hit = active && slot >= 0;
-    if (hit) {
+    if (active) {
       const uint64_t i = ~s.tab[e].nlast;
-      const uint64_t g = b * kSlots + (uint64_t)slot;
-      if (values) copy_row<G, VEC16, false>(value_ptr(t, g), values + i * t.dim, t.dim, lane_g);
-      if (lane_g == 0) {
-        uint64_t m = (uint64_t)s.tab[e].cnt_m1 + 1;
-        uint64_t old = t.scores[g];
-        t.scores[g] = policy_score(t.policy, true, old, m, scores_in != nullptr,
-                                   scores_in ? __ldg(scores_in + i) : 0, ctx);
-        s.tstatus[e] = HKV_ST_UPDATED;
-        updated++;
+      const uint64_t m = (uint64_t)s.tab[e].cnt_m1 + 1;
+      if (hit) {
+        const uint64_t g = b * kSlots + (uint64_t)slot;
+        if (values) copy_row<G, VEC16, false>(value_ptr(t, g), values + i * t.dim, t.dim, lane_g);
+        if (lane_g == 0) {
+          const uint64_t old = t.scores[g];
+          t.scores[g] = policy_score(t.policy, true, old, m, scores_in != nullptr,
+                                     scores_in ? __ldg(scores_in + i) : 0, ctx);
+          s.tstatus[e] = HKV_ST_UPDATED;
+          updated++;
+        }
+      }
+      if (UPSERT && lane_g == 0) {
+        s.mflag[u] = hit ? 0 : 1;
+        if (!hit) {
+          s.mkey[u] = key;
+          s.mi[u] = (uint32_t)i;
+          s.mm[u] = (uint32_t)m;
+        }
       }
     }
-    if (UPSERT) {
-      bool miss = active && !hit && lane_g == 0;
-      unsigned long long q = warp_append(s.cnt + kCntMiss, miss);
-      if (miss) s.mlist[q] = e;
-    }
   }
-  updated = __reduce_add_sync(kFull, updated);
-  lines = __reduce_add_sync(kFull, lines);
-  kreads = __reduce_add_sync(kFull, kreads);
-  if (lane == 0) {
-    count_add(t, HKV_CNT_UPDATED, updated);
-    count_add(t, HKV_CNT_UPD_LINES, lines);
-    count_add(t, HKV_CNT_UPD_KEYS, kreads);
-  }
+  const int which[3] = {HKV_CNT_UPDATED, HKV_CNT_UPD_LINES, HKV_CNT_UPD_KEYS};
+  const unsigned vals[3] = {updated, lines, kreads};
+  flush_counts(t, which, vals);
 }
 
 // --------------------------------------------------------- phase I insert
@@ -239,10 +247,16 @@ constexpr int kInsThreads = 256;
 __device__ __forceinline__ unsigned long long shfl_min_u64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
-    unsigned long long w = __shfl_xor_sync(kFull, v, o);
+    const unsigned long long w = __shfl_xor_sync(kFull, v, o);
     v = w < v ? w : v;
   }
   return v;
+}
+
+// Slot of a bucket held by `lane` in the coalesced score layout: q = 0, 1
+// are slots 2*lane, 2*lane + 1; q = 2, 3 are 64 + 2*lane, 65 + 2*lane.
+__device__ __forceinline__ int held_slot(int lane, int q) {
+  return (q >> 1) * 64 + 2 * lane + (q & 1);
 }
 
 // Write (key, value, score, digest) into a slot this warp holds LOCKED, then
@@ -259,7 +273,7 @@ __device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_
     for (uint32_t j = lane; j < t.dim; j += 32) __stcg(dst + j, __ldg(src + j));
   }
   if (lane == 0) {
-    __stcg(t.scores + g, sc);
+    __stcg(reinterpret_cast<unsigned long long*>(t.scores + g), (unsigned long long)sc);
     t.digests[g] = (uint8_t)dg;
     __threadfence();
     atomicExch(reinterpret_cast<unsigned long long*>(t.keys + g), (unsigned long long)key);
@@ -267,239 +281,236 @@ __device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_
   __syncwarp();
 }
 
-// Re-read the candidate slots (through L2) while holding slot `g` locked
-// with victim (smin, kmin); true iff no other slot precedes or ties it in
-// (score, key) order or is being rewritten. All lanes take part.
-__device__ __forceinline__ bool victim_is_min(const TableDev& t, uint64_t b1, uint64_t b2, bool two,
-                                              uint64_t g, unsigned long long smin,
-                                              unsigned long long kmin, int lane,
-                                              unsigned& kreads) {
-  bool bad = false;
-#pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    if (half == 1 && !two) break;
-    const uint64_t b = half ? b2 : b1;
-    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(t.scores + b * kSlots) + lane * 2;
-    const ulonglong2 a = __ldcg(p), c = __ldcg(p + 1);
-    const unsigned long long sv[4] = {a.x, a.y, c.x, c.y};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint64_t x = b * kSlots + lane * 4 + q;
-      if (x == g) {
-        bad |= sv[q] != smin;
-        continue;
-      }
-      if (sv[q] < smin) { bad = true; continue; }
-      if (sv[q] == smin) {
-        const uint64_t kx = __ldcg(t.keys + x);
-        kreads++;
-        bad |= kx == kLockedKey || kx < kmin;
-      }
-    }
-  }
-  return !__any_sync(kFull, bad);
-}
-
 template <bool VEC16>
-__global__ void __launch_bounds__(kInsThreads)
+__global__ void __launch_bounds__(kInsThreads, 4)
     insert_kernel(TableDev t, Scratch s, const float* __restrict__ values,
                   const uint64_t* __restrict__ scores_in, ScoreCtx ctx) {
   if (aborted(s)) return;
   const int lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * (uint64_t)kInsThreads + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * kInsThreads) >> 5;
-  const uint64_t nm = s.cnt[kCntMiss];
+  const uint64_t nu = s.cnt[kCntUnique];
+  const uint64_t nchunks = (nu + 31) / 32;
   unsigned inserted = 0, evicted = 0, rejected = 0, retries = 0;
   unsigned lines = 0, score_lines = 0, kreads = 0;
 
-  for (uint64_t j = warp; j < nm; j += nwarps) {
-    const uint32_t e = s.mlist[j];
-    const uint64_t key = s.tab[e].key;
-    const uint64_t i = ~s.tab[e].nlast;
-    const uint64_t m = (uint64_t)s.tab[e].cnt_m1 + 1;
-    const uint64_t sc = policy_score(t.policy, false, 0, m, scores_in != nullptr,
-                                     scores_in ? __ldg(scores_in + i) : 0, ctx);
-    const float* src = values + i * t.dim;
-    const uint64_t h = fmix64(key);
-    const uint32_t dg = digest_from_hash(h);
-    const uint64_t b1 = h & t.bucket_mask;
-    const uint64_t b2 = t.dual ? second_bucket(t, key) : b1;
-    const bool two = b2 != b1;
-    uint8_t outcome = HKV_ST_REJECTED;
-    int attempt = 0;
-    for (; attempt < kMaxClaimAttempts; ++attempt) {
-      // back off with per-key jitter so warps colliding on a slot fall apart
-      if (attempt) __nanosleep((32u << (attempt < 6 ? attempt : 6)) + ((unsigned)(h >> 17) & 255u));
-      lines += two ? 2 : 1;
-      const uint32_t w1 = __ldcg(reinterpret_cast<const uint32_t*>(t.digests + b1 * kSlots) + lane);
-      const uint32_t z1 = __vcmpeq4(w1, 0u);
-      const int free1 = __reduce_add_sync(kFull, (unsigned)__popc(z1) >> 3);
-      uint32_t w2 = 0, z2 = 0;
-      int free2 = 0;
-      if (two) {
-        w2 = __ldcg(reinterpret_cast<const uint32_t*>(t.digests + b2 * kSlots) + lane);
-        z2 = __vcmpeq4(w2, 0u);
-        free2 = __reduce_add_sync(kFull, (unsigned)__popc(z2) >> 3);
-      }
-      if (free1 > 0 || free2 > 0) {
-        // Algorithm 2 lines 6-9 / Algorithm 3 phase D1: a free slot of the
-        // less occupied candidate (b1 on equal occupancy).
-        const bool use1 = !two || free1 >= free2;
-        const uint64_t bt = use1 ? b1 : b2;
-        const uint32_t zt = use1 ? z1 : z2;
-        const unsigned bal = __ballot_sync(kFull, zt != 0);
-        const unsigned r = (unsigned)(h >> 44) + (unsigned)attempt * 0x9E3779B9u;
-        const int pick = __fns(bal, 0, (int)(r % (unsigned)__popc(bal)) + 1);
+  for (uint64_t c = warp; c < nchunks; c += nwarps) {
+    // The chunk's 32 distinct keys: flags and miss records, coalesced.
+    const uint64_t my_u = c * 32 + lane;
+    const bool miss = my_u < nu && s.mflag[my_u];
+    uint64_t my_key = 0;
+    uint32_t my_i = 0, my_m = 0, my_e = 0;
+    if (miss) {
+      my_key = s.mkey[my_u];
+      my_i = s.mi[my_u];
+      my_m = s.mm[my_u];
+      my_e = s.ulist[my_u];
+    }
+    unsigned todo = __ballot_sync(kFull, miss);
+    while (todo) {
+      const int src_lane = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint64_t u = c * 32 + src_lane;
+      const uint64_t key = __shfl_sync(kFull, my_key, src_lane);
+      const uint64_t i = __shfl_sync(kFull, my_i, src_lane);
+      const uint64_t m = __shfl_sync(kFull, my_m, src_lane);
+      const uint32_t e = __shfl_sync(kFull, my_e, src_lane);
+      const uint64_t sc = policy_score(t.policy, false, 0, m, scores_in != nullptr,
+                                       scores_in ? __ldg(scores_in + i) : 0, ctx);
+      const float* src = values + i * t.dim;
+      const uint64_t h = fmix64(key);
+      const uint32_t dg = digest_from_hash(h);
+      const uint64_t b1 = h & t.bucket_mask;
+      const uint64_t b2 = t.dual ? second_bucket(t, key) : b1;
+      const bool two = b2 != b1;
+      uint8_t outcome = HKV_ST_REJECTED;
+      uint64_t victim_key = kEmptyKey;
+      int attempt = 0;
+      for (; attempt < kMaxClaimAttempts; ++attempt) {
+        // back off with per-key jitter so warps colliding on a slot fall apart
+        if (attempt) __nanosleep((32u << (attempt < 6 ? attempt : 6)) + ((unsigned)(h >> 17) & 255u));
+        lines += two ? 2 : 1;
+        const uint32_t w1 = __ldcg(reinterpret_cast<const uint32_t*>(t.digests + b1 * kSlots) + lane);
+        const uint32_t z1 = __vcmpeq4(w1, 0u);
+        const int free1 = __reduce_add_sync(kFull, (unsigned)__popc(z1) >> 3);
+        uint32_t z2 = 0;
+        int free2 = 0;
+        if (two) {
+          const uint32_t w2 =
+              __ldcg(reinterpret_cast<const uint32_t*>(t.digests + b2 * kSlots) + lane);
+          z2 = __vcmpeq4(w2, 0u);
+          free2 = __reduce_add_sync(kFull, (unsigned)__popc(z2) >> 3);
+        }
+        if (free1 > 0 || free2 > 0) {
+          // Algorithm 2 lines 6-9 / Algorithm 3 phase D1: a free slot of the
+          // less occupied candidate (b1 on equal occupancy).
+          const bool use1 = !two || free1 >= free2;
+          const uint64_t bt = use1 ? b1 : b2;
+          const uint32_t zt = use1 ? z1 : z2;
+          const unsigned bal = __ballot_sync(kFull, zt != 0);
+          const unsigned r = (unsigned)(h >> 44) + (unsigned)attempt * 0x9E3779B9u;
+          const int pick = __fns(bal, 0, (int)(r % (unsigned)__popc(bal)) + 1);
+          int ok = 0;
+          uint64_t g = 0;
+          if (lane == pick) {
+            const int byte = (__ffs(zt) - 1) >> 3;
+            g = bt * kSlots + (uint64_t)(lane * 4 + byte);
+            ok = atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + g), kEmptyKey,
+                           kLockedKey) == kEmptyKey;
+          }
+          ok = __shfl_sync(kFull, ok, pick);
+          g = __shfl_sync(kFull, g, pick);
+          if (!ok) { retries++; continue; }
+          fill_slot<VEC16>(t, g, key, sc, dg, src, lane);
+          outcome = HKV_ST_INSERTED;
+          inserted++;
+          break;
+        }
+        // Full: minimum (score, key) over the candidate slots (Algorithm 2
+        // line 10; Algorithm 3 phase D2 takes both buckets' slots). Scores
+        // are read as two coalesced 512-B halves per bucket.
+        score_lines += two ? 2 : 1;
+        unsigned long long sv[8];
+        {
+          const ulonglong2* p1 = reinterpret_cast<const ulonglong2*>(t.scores + b1 * kSlots);
+          const ulonglong2 a = __ldcg(p1 + lane), d = __ldcg(p1 + 32 + lane);
+          sv[0] = a.x; sv[1] = a.y; sv[2] = d.x; sv[3] = d.y;
+          if (two) {
+            const ulonglong2* p2 = reinterpret_cast<const ulonglong2*>(t.scores + b2 * kSlots);
+            const ulonglong2 f = __ldcg(p2 + lane), q = __ldcg(p2 + 32 + lane);
+            sv[4] = f.x; sv[5] = f.y; sv[6] = q.x; sv[7] = q.y;
+          } else {
+            sv[4] = sv[5] = sv[6] = sv[7] = ~0ull;
+          }
+        }
+        unsigned long long lmin = sv[0];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) lmin = sv[q] < lmin ? sv[q] : lmin;
+        const unsigned long long smin = shfl_min_u64(lmin);
+        // Tie-break by key among the slots holding the minimum score, reading
+        // key pairs next to each other. A slot locked by another warp is
+        // mid-replacement and its next value is not known yet: re-read later
+        // rather than choose around it.
+        unsigned long long kbest = ~0ull;
+        int qbest = -1;
+        bool busy = false;
+#pragma unroll
+        for (int pr = 0; pr < 4; ++pr) {
+          if (pr >= 2 && !two) break;
+          if (sv[2 * pr] != smin && sv[2 * pr + 1] != smin) continue;
+          const uint64_t bq = pr < 2 ? b1 : b2;
+          const ulonglong2 kp = __ldcg(reinterpret_cast<const ulonglong2*>(t.keys + bq * kSlots) +
+                                       (pr & 1) * 32 + lane);
+          kreads += 2;
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const int q = 2 * pr + h2;
+            const unsigned long long kq = h2 ? kp.y : kp.x;
+            if (sv[q] != smin) continue;
+            if (kq >= kLockedKey) { busy = true; continue; }
+            if (kq < kbest) { kbest = kq; qbest = q; }
+          }
+        }
+        const unsigned long long kmin = shfl_min_u64(kbest);
+        if (__any_sync(kFull, busy) || kmin == ~0ull) { retries++; continue; }
+        // Admission control: admit iff (s, k) > (s_min, k_min).
+        if (!sk_less(smin, kmin, sc, key)) {
+          outcome = HKV_ST_REJECTED;
+          rejected++;
+          break;
+        }
+        const unsigned own = __ballot_sync(kFull, qbest >= 0 && kbest == kmin);
+        const int owner = __ffs(own) - 1;
         int ok = 0;
         uint64_t g = 0;
-        if (lane == pick) {
-          const int byte = (__ffs(zt) - 1) >> 3;
-          g = bt * kSlots + (uint64_t)(lane * 4 + byte);
-          ok = atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + g), kEmptyKey, kLockedKey) ==
-               kEmptyKey;
+        if (lane == owner) {
+          const uint64_t bq = qbest < 4 ? b1 : b2;
+          g = bq * kSlots + (uint64_t)held_slot(lane, qbest & 3);
+          ok = atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + g), kmin, kLockedKey) == kmin;
+          // A score and key read from two different occupants of the slot
+          // would show here as a changed score: release and start over.
+          if (ok && __ldcg(reinterpret_cast<const unsigned long long*>(t.scores + g)) != smin) {
+            atomicExch(reinterpret_cast<unsigned long long*>(t.keys + g), kmin);
+            ok = 0;
+          }
         }
-        ok = __shfl_sync(kFull, ok, pick);
-        g = __shfl_sync(kFull, g, pick);
+        ok = __shfl_sync(kFull, ok, owner);
+        g = __shfl_sync(kFull, g, owner);
         if (!ok) { retries++; continue; }
-        fill_slot<VEC16>(t, g, key, sc, dg, src, lane);
-        outcome = HKV_ST_INSERTED;
-        inserted++;
-        break;
-      }
-      // Full: minimum (score, key) over the candidate slots (Algorithm 2
-      // line 10; Algorithm 3 phase D2 takes both buckets' slots).
-      unsigned long long sv[8];
-      score_lines += two ? 2 : 1;
-      {
-        const ulonglong2* p1 = reinterpret_cast<const ulonglong2*>(t.scores + b1 * kSlots) + lane * 2;
-        ulonglong2 a = __ldcg(p1), c = __ldcg(p1 + 1);
-        sv[0] = a.x; sv[1] = a.y; sv[2] = c.x; sv[3] = c.y;
-        if (two) {
-          const ulonglong2* p2 = reinterpret_cast<const ulonglong2*>(t.scores + b2 * kSlots) + lane * 2;
-          ulonglong2 d = __ldcg(p2), f = __ldcg(p2 + 1);
-          sv[4] = d.x; sv[5] = d.y; sv[6] = f.x; sv[7] = f.y;
-        } else {
-          sv[4] = sv[5] = sv[6] = sv[7] = ~0ull;
+        if (lane == 0) s.evs[u] = smin;
+        if (s.evv) {
+          const float* vsrc = value_ptr(t, g);
+          for (uint32_t d = lane; d < t.dim; d += 32) s.evv[u * t.dim + d] = __ldcg(vsrc + d);
         }
-      }
-      unsigned long long lmin = sv[0];
-#pragma unroll
-      for (int q = 1; q < 8; ++q) lmin = sv[q] < lmin ? sv[q] : lmin;
-      const unsigned long long smin = shfl_min_u64(lmin);
-      // Tie-break by key among the slots holding the minimum score. A slot
-      // locked by another warp is mid-replacement and its next value is not
-      // known yet: re-read later rather than choose around it.
-      unsigned long long kbest = ~0ull;
-      int qbest = -1;
-      bool busy = false;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (q >= 4 && !two) break;
-        if (sv[q] != smin) continue;
-        const uint64_t bq = q < 4 ? b1 : b2;
-        const uint64_t kq = __ldcg(t.keys + bq * kSlots + lane * 4 + (q & 3));
-        kreads++;
-        if (kq >= kLockedKey) { busy = true; continue; }
-        if (kq < kbest) { kbest = kq; qbest = q; }
-      }
-      const unsigned long long kmin = shfl_min_u64(kbest);
-      if (__any_sync(kFull, busy) || kmin == ~0ull) { retries++; continue; }
-      // Admission control: admit iff (s, k) > (s_min, k_min).
-      if (!sk_less(smin, kmin, sc, key)) {
-        outcome = HKV_ST_REJECTED;
-        rejected++;
+        fill_slot<VEC16>(t, g, key, sc, dg, src, lane);
+        victim_key = kmin;
+        outcome = HKV_ST_INSERTED;
+        evicted++;
         break;
       }
-      const unsigned own = __ballot_sync(kFull, qbest >= 0 && kbest == kmin);
-      const int owner = __ffs(own) - 1;
-      int ok = 0;
-      uint64_t g = 0;
-      if (lane == owner) {
-        const uint64_t bq = qbest < 4 ? b1 : b2;
-        g = bq * kSlots + (uint64_t)(lane * 4 + (qbest & 3));
-        ok = atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + g), kmin, kLockedKey) == kmin;
-      }
-      ok = __shfl_sync(kFull, ok, owner);
-      g = __shfl_sync(kFull, g, owner);
-      if (!ok) { retries++; continue; }
-      // Validate under the lock that the victim is still the minimum of the
-      // candidate slots: its score unchanged, no other slot lower, no slot
-      // at the same score with a lower key or a replacement in flight. Slot
-      // values only grow while a bucket is full, so a victim that passes
-      // here is the minimum from now on: this is the claim's linearisation
-      // point.
-      unsigned vreads = 0;  // validation re-reads hit L2: not counted as method traffic
-      if (!victim_is_min(t, b1, b2, two, g, smin, kmin, lane, vreads)) {
-        if (lane == owner) atomicExch(reinterpret_cast<unsigned long long*>(t.keys + g), kmin);
-        retries++;
-        continue;
-      }
-      unsigned long long q = 0;
       if (lane == 0) {
-        q = atomicAdd(s.cnt + kCntEvRaw, 1ull);
-        s.evk[q] = kmin;
-        s.evs[q] = smin;
+        if (attempt == kMaxClaimAttempts) latch_error(t.err, HKV_ERR_TIMEOUT);
+        s.evk[u] = victim_key;
+        s.tstatus[e] = outcome;
       }
-      q = __shfl_sync(kFull, q, 0);
-      if (s.evv) {
-        const float* vsrc = value_ptr(t, g);
-        for (uint32_t d = lane; d < t.dim; d += 32) s.evv[q * t.dim + d] = __ldcg(vsrc + d);
-      }
-      fill_slot<VEC16>(t, g, key, sc, dg, src, lane);
-      outcome = HKV_ST_INSERTED;
-      evicted++;
-      break;
     }
-    if (attempt == kMaxClaimAttempts && lane == 0) latch_error(t.err, HKV_ERR_TIMEOUT);
-    if (lane == 0) s.tstatus[e] = outcome;
   }
-  kreads = __reduce_add_sync(kFull, kreads);
-  if (lane == 0) {
-    count_add(t, HKV_CNT_INSERTED, inserted);
-    count_add(t, HKV_CNT_EVICTED, evicted);
-    count_add(t, HKV_CNT_REJECTED, rejected);
-    count_add(t, HKV_CNT_RETRIES, retries);
-    count_add(t, HKV_CNT_INS_LINES, lines);
-    count_add(t, HKV_CNT_INS_SCORES, score_lines);
-    count_add(t, HKV_CNT_INS_KEYS, kreads);
-  }
+  const int which[7] = {HKV_CNT_INSERTED, HKV_CNT_EVICTED, HKV_CNT_REJECTED, HKV_CNT_RETRIES,
+                        HKV_CNT_INS_LINES, HKV_CNT_INS_SCORES, HKV_CNT_INS_KEYS};
+  const unsigned vals[7] = {lane == 0 ? inserted : 0u, lane == 0 ? evicted : 0u,
+                            lane == 0 ? rejected : 0u, lane == 0 ? retries : 0u,
+                            lane == 0 ? lines : 0u, lane == 0 ? score_lines : 0u, kreads};
+  flush_counts(t, which, vals);
 }
 
 // --------------------------------------------------------------- reconcile
 
-__global__ void reconcile_kernel(TableDev t, Scratch s, uint64_t* __restrict__ ev_keys,
-                                 uint64_t* __restrict__ ev_scores, float* __restrict__ ev_values) {
+constexpr int kRecThreads = 256;
+
+__global__ void __launch_bounds__(kRecThreads)
+    reconcile_kernel(TableDev t, Scratch s, uint64_t* __restrict__ ev_keys,
+                     uint64_t* __restrict__ ev_scores, float* __restrict__ ev_values) {
   if (aborted(s)) return;
-  const uint64_t nraw = s.cnt[kCntEvRaw];
-  for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < nraw;
-       q += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = s.evk[q];
-    uint64_t gp = dedup_pos(k, s.tab_bits);
-    bool in_batch = false;
-    for (;;) {
-      const uint64_t tk = s.tab[gp].key;
-      if (tk == k) { in_batch = true; break; }
-      if (tk == kEmptyKey) break;
-      gp = (gp + 1) & s.tab_mask;
+  const uint64_t nu = s.cnt[kCntUnique];
+  for (uint64_t base = (uint64_t)blockIdx.x * kRecThreads; base < nu;
+       base += (uint64_t)gridDim.x * kRecThreads) {
+    const uint64_t u = base + threadIdx.x;
+    uint64_t k = kEmptyKey;
+    if (u < nu && s.mflag[u]) k = s.evk[u];
+    bool out = k != kEmptyKey;
+    if (out) {
+      uint64_t gp = dedup_pos(k, s.tab_bits);
+      for (;;) {
+        const uint64_t tk = s.tab[gp].key;
+        if (tk == k) {
+          // displaced by a later key of this batch: not an eviction
+          if (s.tstatus[gp] == HKV_ST_INSERTED) {
+            s.tstatus[gp] = HKV_ST_REJECTED;
+            out = false;
+          }
+          break;
+        }
+        if (tk == kEmptyKey) break;
+        gp = (gp + 1) & s.tab_mask;
+      }
     }
-    if (in_batch && s.tstatus[gp] == HKV_ST_INSERTED) {
-      s.tstatus[gp] = HKV_ST_REJECTED;  // displaced by a later key of this batch
-      continue;
+    const unsigned long long o = block_reserve(s.cnt + kCntEvOut, out ? 1u : 0u);
+    if (out) {
+      if (ev_keys) ev_keys[o] = k;
+      if (ev_scores) ev_scores[o] = s.evs[u];
+      if (ev_values && s.evv)
+        for (uint32_t d = 0; d < t.dim; ++d) ev_values[o * t.dim + d] = s.evv[u * t.dim + d];
     }
-    const unsigned long long o = atomicAdd(s.cnt + kCntEvOut, 1ull);
-    if (ev_keys) ev_keys[o] = k;
-    if (ev_scores) ev_scores[o] = s.evs[q];
-    if (ev_values && s.evv)
-      for (uint32_t d = 0; d < t.dim; ++d) ev_values[o * t.dim + d] = s.evv[q * t.dim + d];
   }
 }
 
 __global__ void status_kernel(uint64_t n, Scratch s, uint8_t* __restrict__ status_out,
                               uint64_t* __restrict__ n_evicted) {
   if (aborted(s)) return;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x)
-    if (status_out) status_out[i] = s.tstatus[s.slot_of[i]];
+  if (status_out)
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+      status_out[i] = s.tstatus[s.slot_of[i]];
   if (n_evicted && blockIdx.x == 0 && threadIdx.x == 0) *n_evicted = s.cnt[kCntEvOut];
 }
 
@@ -538,8 +549,8 @@ __global__ void __launch_bounds__(kUpdThreads)
       const uint64_t b2 = second_bucket(t, key);
       const bool need = active && slot < 0 && b2 != b;
       if (__any_sync(kFull, need)) {
-        int s2 = probe_bucket<G, true>(t, b2, key, pat4, need, lane_g, group_bits, group_base,
-                                       kreads);
+        const int s2 = probe_bucket<G, true>(t, b2, key, pat4, need, lane_g, group_bits,
+                                             group_base, kreads);
         if (need && s2 >= 0) { slot = s2; b = b2; }
       }
     }
@@ -561,18 +572,20 @@ struct ScratchAlloc {
 
 uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
-hkv_status alloc_scratch(hkv_table_s* t, uint64_t n, bool want_ev_values, cudaStream_t st,
-                         ScratchAlloc* a) {
+hkv_status alloc_scratch(hkv_table_s* t, uint64_t n, bool upsert, bool want_ev_values,
+                         cudaStream_t st, ScratchAlloc* a) {
   int bits = 10;
   while ((1ull << bits) < 2 * n) ++bits;
   const uint64_t T = 1ull << bits;
   const uint64_t sz_tab = align256(T * sizeof(DedupEntry));
   const uint64_t sz_ts = align256(T);
+  const uint64_t sz_u8 = align256(n);
   const uint64_t sz_u32 = align256(n * 4);
-  const uint64_t sz_cnt = align256(kCntWords * 8);
   const uint64_t sz_u64 = align256(n * 8);
+  const uint64_t sz_cnt = align256(kCntWords * 8);
   const uint64_t sz_evv = want_ev_values ? align256(n * (uint64_t)t->dev.dim * 4) : 0;
-  const uint64_t total = sz_tab + sz_ts + 3 * sz_u32 + sz_cnt + 2 * sz_u64 + sz_evv;
+  uint64_t total = sz_tab + sz_ts + 2 * sz_u32 + sz_cnt;
+  if (upsert) total += sz_u8 + 3 * sz_u64 + 2 * sz_u32 + sz_evv;
   cudaError_t e = cudaMallocFromPoolAsync(&a->base, total, t->pool, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -587,11 +600,16 @@ hkv_status alloc_scratch(hkv_table_s* t, uint64_t n, bool want_ev_values, cudaSt
   s.tstatus = reinterpret_cast<uint8_t*>(p); p += sz_ts;
   s.slot_of = reinterpret_cast<uint32_t*>(p); p += sz_u32;
   s.ulist = reinterpret_cast<uint32_t*>(p); p += sz_u32;
-  s.mlist = reinterpret_cast<uint32_t*>(p); p += sz_u32;
   s.cnt = reinterpret_cast<unsigned long long*>(p); p += sz_cnt;
-  s.evk = reinterpret_cast<uint64_t*>(p); p += sz_u64;
-  s.evs = reinterpret_cast<uint64_t*>(p); p += sz_u64;
-  s.evv = want_ev_values ? reinterpret_cast<float*>(p) : nullptr;
+  if (upsert) {
+    s.mflag = reinterpret_cast<uint8_t*>(p); p += sz_u8;
+    s.mkey = reinterpret_cast<uint64_t*>(p); p += sz_u64;
+    s.evk = reinterpret_cast<uint64_t*>(p); p += sz_u64;
+    s.evs = reinterpret_cast<uint64_t*>(p); p += sz_u64;
+    s.mi = reinterpret_cast<uint32_t*>(p); p += sz_u32;
+    s.mm = reinterpret_cast<uint32_t*>(p); p += sz_u32;
+    s.evv = want_ev_values ? reinterpret_cast<float*>(p) : nullptr;
+  }
   cudaMemsetAsync(s.tab, 0xFF, T * sizeof(DedupEntry), st);
   cudaMemsetAsync(s.cnt, 0, kCntWords * 8, st);
   return HKV_OK;
@@ -599,7 +617,7 @@ hkv_status alloc_scratch(hkv_table_s* t, uint64_t n, bool want_ev_values, cudaSt
 
 unsigned grid_for(const hkv_table_s* t, uint64_t threads_needed, int block, int per_sm) {
   uint64_t blocks = (threads_needed + block - 1) / block;
-  uint64_t cap = (uint64_t)t->num_sms * per_sm;
+  const uint64_t cap = (uint64_t)t->num_sms * per_sm;
   if (blocks > cap) blocks = cap;
   return blocks ? (unsigned)blocks : 1u;
 }
@@ -632,18 +650,10 @@ void launch_dedup(hkv_table_s* t, uint64_t n, const uint64_t* keys, const Scratc
                   cudaStream_t st) {
   const unsigned grid = (unsigned)((n + kDedupTile - 1) / kDedupTile);
   KernelTimer timer(t->prof, HKV_K_DEDUP, st);
-  dedup_kernel<<<grid, kDedupThreads, kDedupSmem, st>>>(n, keys, s, t->dev.err,
-                                                        t->opts.deterministic, s.cnt + kCntUnique,
-                                                        t->dev);
+  dedup_kernel<<<grid, kDedupThreads, kDedupSmem, st>>>(n, keys, s, t->dev, t->opts.deterministic);
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
-
-struct DedupSmemInit {
-  DedupSmemInit() {
-    cudaFuncSetAttribute(dedup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDedupSmem);
-  }
-};
 
 }  // namespace
 
@@ -651,21 +661,19 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
                          const uint64_t* scores, uint8_t* status_out, uint64_t* ev_keys,
                          uint64_t* ev_scores, float* ev_values, uint64_t* n_evicted,
                          ScoreCtx ctx, cudaStream_t st) {
-  static DedupSmemInit init_once;
-  (void)init_once;
   if (n == 0) {
     if (n_evicted) cudaMemsetAsync(n_evicted, 0, 8, st);
     return cuda_status(cudaGetLastError(), "upsert");
   }
   ScratchAlloc a;
-  hkv_status rc = alloc_scratch(t, n, ev_values != nullptr, st, &a);
+  hkv_status rc = alloc_scratch(t, n, true, ev_values != nullptr, st, &a);
   if (rc) return rc;
   const Scratch& s = a.s;
   const bool vec16 = t->dev.dim % 4 == 0 && aligned16(values);
   launch_dedup(t, n, keys, s, st);
   launch_update<true>(t, n, s, values, scores, ctx, vec16, st);
-  const unsigned ig = grid_for(t, n * 32, kInsThreads, 2048 / kInsThreads);
   {
+    const unsigned ig = grid_for(t, (n + 31) / 32 * 32, kInsThreads, 4);
     KernelTimer timer(t->prof, HKV_K_INSERT, st);
     if (vec16)
       insert_kernel<true><<<ig, kInsThreads, 0, st>>>(t->dev, s, values, scores, ctx);
@@ -674,8 +682,8 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
   }
   {
     KernelTimer timer(t->prof, HKV_K_RECONCILE, st);
-    reconcile_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(t->dev, s, ev_keys, ev_scores,
-                                                              ev_values);
+    reconcile_kernel<<<grid_for(t, n, kRecThreads, 8), kRecThreads, 0, st>>>(
+        t->dev, s, ev_keys, ev_scores, ev_values);
   }
   if (status_out || n_evicted) {
     KernelTimer timer(t->prof, HKV_K_STATUS, st);
@@ -687,11 +695,9 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
 
 hkv_status launch_assign(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,
                          const uint64_t* scores, ScoreCtx ctx, cudaStream_t st) {
-  static DedupSmemInit init_once;
-  (void)init_once;
   if (n == 0) return HKV_OK;
   ScratchAlloc a;
-  hkv_status rc = alloc_scratch(t, n, false, st, &a);
+  hkv_status rc = alloc_scratch(t, n, false, false, st, &a);
   if (rc) return rc;
   const bool vec16 = t->dev.dim % 4 == 0 && (values == nullptr || aligned16(values));
   launch_dedup(t, n, keys, a.s, st);
