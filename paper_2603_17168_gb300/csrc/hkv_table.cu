@@ -267,10 +267,11 @@ hkv_status hkv_create(const hkv_options* o, hkv_table_t* out) {
                                                          t->dev.scores, slots);
   cudaMemset(t->dev.err, 0, 256);
   cudaMemset(t->dev.counters, 0, 256);
-  if (t->opts.dim >= 64) {
-    t->launch.find_tpk = 16;
-    t->launch.update_tpk = 16;
-  }
+  // Default launch shape (the autotuner refines it per table): few threads
+  // per key keep the probe kernels from being issue-bound; wide values get
+  // more lanes for the row copy.
+  t->launch.find_tpk = t->opts.dim <= 32 ? 2 : (t->opts.dim <= 128 ? 4 : 8);
+  t->launch.update_tpk = t->opts.dim <= 32 ? 1 : (t->opts.dim <= 128 ? 2 : 4);
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     free_table(t);

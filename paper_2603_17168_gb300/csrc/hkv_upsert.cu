@@ -10,12 +10,14 @@
 //   update    phase U: probe every distinct key (G lanes per key, digest
 //             line + key confirm) and update residents in place; a miss
 //             leaves (key, source row, multiplicity) at its index u;
-//   insert    phase I: a warp takes 32 consecutive u, and for each miss
-//             claims a free slot with a CAS on the key word (EMPTY ->
-//             LOCKED), or, when the bucket (both buckets in dual mode) is
-//             full, reduces the minimum (score, key) over the 128 (256)
-//             slots, applies admission control, CAS-locks the victim and
-//             replaces it (Algorithm 2 lines 6-14, Algorithm 3);
+//   insert    phase I: a warp takes 32 consecutive u. Each thread claims
+//             a free slot for its own miss with a CAS on the key word
+//             (EMPTY -> LOCKED); keys whose bucket (both buckets in dual
+//             mode) is full then get a warp-cooperative victim search that
+//             reduces the minimum (score, key) over the 128 (256) slots,
+//             applies admission control, CAS-locks the victim and replaces
+//             it (Algorithm 2 lines 6-14, Algorithm 3). The next searches'
+//             score and key lines are bulk-prefetched into L2;
 //   reconcile a victim that was itself inserted by this batch is not an
 //             eviction: its key becomes REJECTED and it is dropped from the
 //             evicted output, which is compacted here;
@@ -281,6 +283,56 @@ __device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_
   __syncwarp();
 }
 
+// L2 prefetch of a contiguous range with one TMA bulk instruction
+// (cp.async.bulk.prefetch.L2; size a multiple of 16 bytes).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Free slots of a bucket as seen by one thread: count, and one candidate
+// found by scanning the 16-byte pieces of the digest line from a
+// key-dependent start (so keys of one bucket rarely pick the same slot).
+__device__ __forceinline__ void scan_free(const uint8_t* line, unsigned start, int& nfree, int& cand) {
+  const uint4* p = reinterpret_cast<const uint4*>(line);
+  uint4 v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = __ldcg(p + q);
+  nfree = 0;
+  cand = -1;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int q = (k + start) & 7;
+    const uint32_t w[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t z = __vcmpeq4(w[j], 0u);
+      nfree += __popc(z) >> 3;
+      if (cand < 0 && z) cand = q * 16 + j * 4 + ((__ffs(z) - 1) >> 3);
+    }
+  }
+}
+
+// One thread writes (value, score, digest) into a slot it holds LOCKED and
+// publishes the key.
+template <bool VEC16>
+__device__ __forceinline__ void fill_slot_thread(const TableDev& t, uint64_t g, uint64_t key,
+                                                 uint64_t sc, uint32_t dg, const float* src) {
+  float* dst = value_ptr(t, g);
+  if (VEC16) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (uint32_t j = 0; j < (t.dim >> 2); ++j) __stcg(d4 + j, __ldg(s4 + j));
+  } else {
+    for (uint32_t j = 0; j < t.dim; ++j) __stcg(dst + j, __ldg(src + j));
+  }
+  __stcg(reinterpret_cast<unsigned long long*>(t.scores + g), (unsigned long long)sc);
+  t.digests[g] = (uint8_t)dg;
+  __threadfence();
+  atomicExch(reinterpret_cast<unsigned long long*>(t.keys + g), (unsigned long long)key);
+}
+
+constexpr int kPrefetchAhead = 3;  // victim searches whose lines are prefetched ahead
+
 template <bool VEC16>
 __global__ void __launch_bounds__(kInsThreads, 4)
     insert_kernel(TableDev t, Scratch s, const float* __restrict__ values,
@@ -306,69 +358,108 @@ __global__ void __launch_bounds__(kInsThreads, 4)
       my_m = s.mm[my_u];
       my_e = s.ulist[my_u];
     }
-    unsigned todo = __ballot_sync(kFull, miss);
+    const uint64_t my_h = fmix64(my_key);
+    const uint64_t my_b1 = my_h & t.bucket_mask;
+    const uint64_t my_b2 = t.dual ? second_bucket(t, my_key) : my_b1;
+    const bool my_two = my_b2 != my_b1;
+    const uint64_t my_sc = policy_score(t.policy, false, 0, my_m, scores_in != nullptr,
+                                        (miss && scores_in) ? __ldg(scores_in + my_i) : 0, ctx);
+
+    // Phase A, one thread per key: claim a free slot of the less occupied
+    // candidate (Algorithm 2 lines 6-9; Algorithm 3 phase D1). Keys whose
+    // candidates are all full go on to the victim search.
+    bool pending = miss, full = false;
+    for (int attempt = 0; __any_sync(kFull, pending) && attempt < kMaxClaimAttempts; ++attempt) {
+      if (!pending) continue;
+      if (attempt) __nanosleep((32u << (attempt < 6 ? attempt : 6)) + ((unsigned)(my_h >> 17) & 255u));
+      const unsigned start = (unsigned)(my_h >> 40) + (unsigned)attempt;
+      int f1, c1, f2 = 0, c2 = -1;
+      scan_free(t.digests + my_b1 * kSlots, start, f1, c1);
+      lines++;
+      if (my_two) {
+        scan_free(t.digests + my_b2 * kSlots, start, f2, c2);
+        lines++;
+      }
+      if (f1 == 0 && f2 == 0) {
+        pending = false;
+        full = true;
+        continue;
+      }
+      const bool use1 = !my_two || f1 >= f2;
+      const uint64_t g = (use1 ? my_b1 : my_b2) * kSlots + (uint64_t)(use1 ? c1 : c2);
+      if (atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + g), kEmptyKey, kLockedKey) !=
+          kEmptyKey) {
+        retries++;
+        continue;
+      }
+      fill_slot_thread<VEC16>(t, g, my_key, my_sc, digest_from_hash(my_h), values + my_i * t.dim);
+      pending = false;
+      inserted++;
+      s.evk[my_u] = kEmptyKey;
+      s.tstatus[my_e] = HKV_ST_INSERTED;
+    }
+    if (pending) {  // bounded wait ran out
+      latch_error(t.err, HKV_ERR_TIMEOUT);
+      s.evk[my_u] = kEmptyKey;
+      s.tstatus[my_e] = HKV_ST_REJECTED;
+    }
+
+    // Phase B, warp-cooperative victim search for the keys whose buckets
+    // were full. The score and key lines of the next searches are pulled
+    // into L2 by bulk prefetches while the current one runs.
+    unsigned todo = __ballot_sync(kFull, full);
+    {
+      unsigned ahead = todo;
+      for (int k = 0; k < kPrefetchAhead && ahead; ++k) {
+        const int l = __ffs(ahead) - 1;
+        ahead &= ahead - 1;
+        if (lane == l) {
+          bulk_prefetch_l2(t.scores + my_b1 * kSlots, kSlots * 8);
+          bulk_prefetch_l2(t.keys + my_b1 * kSlots, kSlots * 8);
+          if (my_two) {
+            bulk_prefetch_l2(t.scores + my_b2 * kSlots, kSlots * 8);
+            bulk_prefetch_l2(t.keys + my_b2 * kSlots, kSlots * 8);
+          }
+        }
+      }
+    }
     while (todo) {
       const int src_lane = __ffs(todo) - 1;
       todo &= todo - 1;
+      {
+        // prefetch the search kPrefetchAhead positions ahead
+        unsigned ahead = todo;
+        for (int k = 1; k < kPrefetchAhead && ahead; ++k) ahead &= ahead - 1;
+        if (ahead) {
+          const int l = __ffs(ahead) - 1;
+          if (lane == l) {
+            bulk_prefetch_l2(t.scores + my_b1 * kSlots, kSlots * 8);
+            bulk_prefetch_l2(t.keys + my_b1 * kSlots, kSlots * 8);
+            if (my_two) {
+              bulk_prefetch_l2(t.scores + my_b2 * kSlots, kSlots * 8);
+              bulk_prefetch_l2(t.keys + my_b2 * kSlots, kSlots * 8);
+            }
+          }
+        }
+      }
       const uint64_t u = c * 32 + src_lane;
       const uint64_t key = __shfl_sync(kFull, my_key, src_lane);
       const uint64_t i = __shfl_sync(kFull, my_i, src_lane);
-      const uint64_t m = __shfl_sync(kFull, my_m, src_lane);
       const uint32_t e = __shfl_sync(kFull, my_e, src_lane);
-      const uint64_t sc = policy_score(t.policy, false, 0, m, scores_in != nullptr,
-                                       scores_in ? __ldg(scores_in + i) : 0, ctx);
-      const float* src = values + i * t.dim;
-      const uint64_t h = fmix64(key);
-      const uint32_t dg = digest_from_hash(h);
-      const uint64_t b1 = h & t.bucket_mask;
-      const uint64_t b2 = t.dual ? second_bucket(t, key) : b1;
+      const uint64_t sc = __shfl_sync(kFull, my_sc, src_lane);
+      const uint64_t h = __shfl_sync(kFull, my_h, src_lane);
+      const uint64_t b1 = __shfl_sync(kFull, my_b1, src_lane);
+      const uint64_t b2 = __shfl_sync(kFull, my_b2, src_lane);
       const bool two = b2 != b1;
+      const float* src = values + i * t.dim;
+      const uint32_t dg = digest_from_hash(h);
       uint8_t outcome = HKV_ST_REJECTED;
       uint64_t victim_key = kEmptyKey;
       int attempt = 0;
       for (; attempt < kMaxClaimAttempts; ++attempt) {
-        // back off with per-key jitter so warps colliding on a slot fall apart
         if (attempt) __nanosleep((32u << (attempt < 6 ? attempt : 6)) + ((unsigned)(h >> 17) & 255u));
-        lines += two ? 2 : 1;
-        const uint32_t w1 = __ldcg(reinterpret_cast<const uint32_t*>(t.digests + b1 * kSlots) + lane);
-        const uint32_t z1 = __vcmpeq4(w1, 0u);
-        const int free1 = __reduce_add_sync(kFull, (unsigned)__popc(z1) >> 3);
-        uint32_t z2 = 0;
-        int free2 = 0;
-        if (two) {
-          const uint32_t w2 =
-              __ldcg(reinterpret_cast<const uint32_t*>(t.digests + b2 * kSlots) + lane);
-          z2 = __vcmpeq4(w2, 0u);
-          free2 = __reduce_add_sync(kFull, (unsigned)__popc(z2) >> 3);
-        }
-        if (free1 > 0 || free2 > 0) {
-          // Algorithm 2 lines 6-9 / Algorithm 3 phase D1: a free slot of the
-          // less occupied candidate (b1 on equal occupancy).
-          const bool use1 = !two || free1 >= free2;
-          const uint64_t bt = use1 ? b1 : b2;
-          const uint32_t zt = use1 ? z1 : z2;
-          const unsigned bal = __ballot_sync(kFull, zt != 0);
-          const unsigned r = (unsigned)(h >> 44) + (unsigned)attempt * 0x9E3779B9u;
-          const int pick = __fns(bal, 0, (int)(r % (unsigned)__popc(bal)) + 1);
-          int ok = 0;
-          uint64_t g = 0;
-          if (lane == pick) {
-            const int byte = (__ffs(zt) - 1) >> 3;
-            g = bt * kSlots + (uint64_t)(lane * 4 + byte);
-            ok = atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + g), kEmptyKey,
-                           kLockedKey) == kEmptyKey;
-          }
-          ok = __shfl_sync(kFull, ok, pick);
-          g = __shfl_sync(kFull, g, pick);
-          if (!ok) { retries++; continue; }
-          fill_slot<VEC16>(t, g, key, sc, dg, src, lane);
-          outcome = HKV_ST_INSERTED;
-          inserted++;
-          break;
-        }
-        // Full: minimum (score, key) over the candidate slots (Algorithm 2
-        // line 10; Algorithm 3 phase D2 takes both buckets' slots). Scores
-        // are read as two coalesced 512-B halves per bucket.
+        // Buckets stay full during a batch (no erase runs beside an
+        // inserter), so the victim search needs no free-slot re-check.
         score_lines += two ? 2 : 1;
         unsigned long long sv[8];
         {
@@ -412,7 +503,7 @@ __global__ void __launch_bounds__(kInsThreads, 4)
           }
         }
         const unsigned long long kmin = shfl_min_u64(kbest);
-        if (__any_sync(kFull, busy) || kmin == ~0ull) { retries++; continue; }
+        if (__any_sync(kFull, busy) || kmin == ~0ull) { retries += lane == 0; continue; }
         // Admission control: admit iff (s, k) > (s_min, k_min).
         if (!sk_less(smin, kmin, sc, key)) {
           outcome = HKV_ST_REJECTED;
@@ -436,7 +527,7 @@ __global__ void __launch_bounds__(kInsThreads, 4)
         }
         ok = __shfl_sync(kFull, ok, owner);
         g = __shfl_sync(kFull, g, owner);
-        if (!ok) { retries++; continue; }
+        if (!ok) { retries += lane == 0; continue; }
         if (lane == 0) s.evs[u] = smin;
         if (s.evv) {
           const float* vsrc = value_ptr(t, g);
@@ -457,9 +548,8 @@ __global__ void __launch_bounds__(kInsThreads, 4)
   }
   const int which[7] = {HKV_CNT_INSERTED, HKV_CNT_EVICTED, HKV_CNT_REJECTED, HKV_CNT_RETRIES,
                         HKV_CNT_INS_LINES, HKV_CNT_INS_SCORES, HKV_CNT_INS_KEYS};
-  const unsigned vals[7] = {lane == 0 ? inserted : 0u, lane == 0 ? evicted : 0u,
-                            lane == 0 ? rejected : 0u, lane == 0 ? retries : 0u,
-                            lane == 0 ? lines : 0u, lane == 0 ? score_lines : 0u, kreads};
+  const unsigned vals[7] = {inserted, lane == 0 ? evicted : 0u, lane == 0 ? rejected : 0u,
+                            retries, lines, lane == 0 ? score_lines : 0u, kreads};
   flush_counts(t, which, vals);
 }
 
@@ -648,6 +738,9 @@ void launch_update(hkv_table_s* t, uint64_t n, const Scratch& s, const float* va
 
 void launch_dedup(hkv_table_s* t, uint64_t n, const uint64_t* keys, const Scratch& s,
                   cudaStream_t st) {
+  static const cudaError_t smem_ok = cudaFuncSetAttribute(
+      dedup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDedupSmem);
+  (void)smem_ok;
   const unsigned grid = (unsigned)((n + kDedupTile - 1) / kDedupTile);
   KernelTimer timer(t->prof, HKV_K_DEDUP, st);
   dedup_kernel<<<grid, kDedupThreads, kDedupSmem, st>>>(n, keys, s, t->dev, t->opts.deterministic);
