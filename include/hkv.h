@@ -55,7 +55,7 @@ typedef enum {
   HKV_ERR_BUSY = 7
 } hkv_status;
 
-/* Score policies (Sec. 3.3, "Scoring policies"; Table 5). The paper names
+/* Score policies (Sec. 3.3, "Scoring policies"; Table 8, cache hit rate by policy). The paper names
  * them without formulas; this library defines, per insert_or_assign or
  * assign call (the table step advances by one at the start of each):
  *   HKV_LRU            score = step, for new and updated keys;

@@ -11,9 +11,9 @@ Parity status of each function (pins are in tests/test_oracle_*.py):
                                     uniformity, first-eviction band)
   find / contains                   pinned (brute-force scan, Prop. 1 count)
   insert_or_assign, single bucket   pinned (closed-form top-S, permutation
-                                    invariance, B = 1 top-k, Tab. 6 burst)
+                                    invariance, B = 1 top-k, Table 9 admission burst)
   insert_or_assign, dual bucket     pinned (Prop. 3 order statistic,
-                                    first-eviction band of Tab. 8, invariants)
+                                    first-eviction band of Table 11, invariants)
   assign / erase / export / load    pinned (brute-force model, round trip)
   score policies                    pinned (closed-form counts per policy)
 """

@@ -1,5 +1,5 @@
 """Pins of the oracle's dual-bucket selection (Algorithm 3, Proposition 3,
-Table 8) and of single-bucket first eviction (Sec. 3.4, Table 8)."""
+Table 11) and of single-bucket first eviction (Sec. 3.4, Table 11)."""
 import json
 import os
 
@@ -85,7 +85,7 @@ def test_first_eviction_single_matches_balls_in_bins():
     # eviction comes when the fullest bucket receives its 129th key. Under the
     # Poisson approximation P(no overflow at load lambda) =
     # P(Pois(128 lambda) <= 128)^B; its median is the expected point. The paper
-    # reports 0.633 at B = 2^20 (Table 8) and ~0.66 in Sec. 3.4.
+    # reports 0.633 at B = 2^20 (Table 11) and ~0.66 in Sec. 3.4.
     nb = 1 << 12
     lam = np.linspace(0.4, 0.95, 2000)
     p_ok = stats.poisson.cdf(128, 128 * lam) ** nb
@@ -101,8 +101,8 @@ def test_first_eviction_single_matches_balls_in_bins():
     assert abs(m20 - g["value"]) < 0.03
 
 
-def test_first_eviction_dual_table8_band():
-    # Table 8: phase D1 delays the first eviction to lambda ~ 0.977.
+def test_first_eviction_dual_table11_band():
+    # Table 11: phase D1 delays the first eviction to lambda ~ 0.977.
     got = first_eviction_lambda(1 << 12, True, 902)
     assert abs(got - GOLD["first_eviction_lambda_dual"]["value"]) < 0.02, got
 

@@ -1,5 +1,5 @@
 """Pins of the oracle's insert_or_assign / assign / erase (Algorithm 2,
-Sec. 3.3; Table 6; the batch semantics stated in oracle/hkv_oracle.c)."""
+Sec. 3.3; Table 9 (admission burst, Exp. 3d); the batch semantics stated in oracle/hkv_oracle.c)."""
 import heapq
 
 import numpy as np
@@ -123,8 +123,8 @@ def full_table(nb, rng, dim=1, lo=2, hi=10**8):
     return t
 
 
-def test_admission_burst_table6():
-    # Table 6: a low-score burst is fully rejected and leaves the table as it
+def test_admission_burst_table9():
+    # Table 9 (Exp. 3d): a low-score burst is fully rejected and leaves the table as it
     # was; a high-score burst is fully admitted, each key displacing an
     # original. Scaled to a full 2^17-slot table (the paper's 16M slots at
     # lambda = 0.96 still has free slots, which admit regardless of score).
