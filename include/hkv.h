@@ -147,6 +147,35 @@ hkv_status hkv_insert_or_assign(hkv_table_t t, uint64_t n, const uint64_t *keys,
                                 uint64_t *evicted_scores, float *evicted_values,
                                 uint64_t *n_evicted, hkv_stream_t stream);
 
+/* insert_or_assign for callers that cannot allocate device memory. The
+ * paper has no counterpart; this library adds it. hkv_insert_or_assign takes
+ * its per-call scratch (about 75 bytes per key) from a stream-ordered pool,
+ * which may allocate. A process whose device memory is all reserved up front
+ * by its framework's allocator, or a latency-critical path that must not
+ * meet an allocation's possible synchronisation or out-of-memory failure,
+ * can call this variant instead: it runs the same kernels with the same
+ * results (except that evicted values are not returned) in one fixed
+ * scratch array of 5 MiB that lives in the library's device image, and it
+ * allocates no memory (no cudaMalloc, cudaFree or pool allocation). Like
+ * every call it records a CUDA event for cross-stream ordering, reusing the
+ * table's event objects.
+ *   n           at most HKV_NOALLOC_MAX_KEYS; larger batches are refused
+ *               with HKV_ERR_INVALID_ARG (split them, or use the pooled call).
+ *   the table's device must be current.
+ * Every GPU that loads the library holds the 5 MiB array until the process
+ * exits. The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls on a device share the one array, and each call overwrites it:
+ * calls that can overlap on that GPU (issued on different streams, even for
+ * different tables) race and must be ordered by the caller. Other
+ * arguments and results are as in hkv_insert_or_assign. */
+#define HKV_NOALLOC_MAX_KEYS 65536u
+hkv_status hkv_insert_or_assign_noalloc(hkv_table_t t, uint64_t n, const uint64_t *keys,
+                                        const float *values, const uint64_t *scores,
+                                        uint8_t *status_out, uint64_t *evicted_keys,
+                                        uint64_t *evicted_scores, uint64_t *n_evicted,
+                                        hkv_stream_t stream);
+
 /* assign (updater; Sec. 3.5): for each resident key, overwrite its value
  * (last occurrence wins) and score per the policy; HKV_CUSTOM takes scores[]
  * when given, else keeps the old score. Missing keys are ignored; the bucket

@@ -26,6 +26,7 @@ KERNEL_NAMES = ("find", "dedup", "update", "insert", "reconcile", "status", "era
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "RESERVED_KEY", 3: "DUPLICATE_KEY", 4: "OOM",
                 5: "CUDA", 6: "TIMEOUT", 7: "BUSY"}
 SLOTS = 128
+NOALLOC_MAX_KEYS = 65536
 
 # Every C-ABI entry point declared in include/hkv.h with its ctypes signature.
 _u64, _u32, _i32, _vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p
@@ -47,6 +48,7 @@ SIGNATURES = {
     "hkv_find": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp, _vp]),
     "hkv_contains": (_i32, [_vp, _u64, _vp, _vp, _vp]),
     "hkv_insert_or_assign": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "hkv_insert_or_assign_noalloc": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hkv_assign": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp]),
     "hkv_erase": (_i32, [_vp, _u64, _vp, _vp]),
     "hkv_size": (_i32, [_vp, _P64, _vp]),
@@ -221,6 +223,26 @@ class Table:
             self._h, n, _ptr(keys), _ptr(values), _ptr(scores), _ptr(status_out),
             _ptr(evicted_keys), _ptr(evicted_scores), _ptr(evicted_values), _ptr(n_evicted),
             _stream(stream)))
+        return status_out
+
+    def insert_or_assign_noalloc(self, keys, values, scores=None, status_out=None,
+                                 evicted_keys=None, evicted_scores=None, n_evicted=None,
+                                 stream=None):
+        """insert_or_assign without any allocation inside the call (see
+        hkv_insert_or_assign_noalloc in include/hkv.h): at most
+        NOALLOC_MAX_KEYS keys, no evicted values."""
+        import torch
+        n = keys.numel()
+        _need(keys, _u64_types(), (n,), "keys")
+        _need(values, torch.float32, (n, self.dim), "values")
+        _need(scores, _u64_types(), (n,), "scores")
+        _need(status_out, torch.uint8, (n,), "status_out")
+        _need(evicted_keys, _u64_types(), None, "evicted_keys")
+        _need(evicted_scores, _u64_types(), None, "evicted_scores")
+        _need(n_evicted, _u64_types(), (1,), "n_evicted")
+        _check(load_library().hkv_insert_or_assign_noalloc(
+            self._h, n, _ptr(keys), _ptr(values), _ptr(scores), _ptr(status_out),
+            _ptr(evicted_keys), _ptr(evicted_scores), _ptr(n_evicted), _stream(stream)))
         return status_out
 
     def assign(self, keys, values=None, scores=None, stream=None):

@@ -133,6 +133,12 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
                          const uint64_t* scores, uint8_t* status_out, uint64_t* ev_keys,
                          uint64_t* ev_scores, float* ev_values, uint64_t* n_evicted,
                          ScoreCtx ctx, cudaStream_t s);
+// The upsert pipeline run in a caller-provided scratch block of
+// scratch_bytes (device memory); no allocation. Evicted values not kept.
+hkv_status launch_upsert_in(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,
+                            const uint64_t* scores, uint8_t* status_out, uint64_t* ev_keys,
+                            uint64_t* ev_scores, uint64_t* n_evicted, ScoreCtx ctx,
+                            void* scratch, uint64_t scratch_bytes, cudaStream_t s);
 hkv_status launch_assign(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,
                          const uint64_t* scores, ScoreCtx ctx, cudaStream_t s);
 hkv_status launch_erase(hkv_table_s* t, uint64_t n, const uint64_t* keys, cudaStream_t s);

@@ -820,3 +820,86 @@ hkv_status launch_erase(hkv_table_s* t, uint64_t n, const uint64_t* keys, cudaSt
 }
 
 }  // namespace hkv
+
+// ------------------------------------------- upsert into caller-given scratch
+
+namespace hkv {
+namespace {
+
+// Lay the per-call scratch out in a caller-provided block (no allocation);
+// returns false if the block is too small. Evicted values are not kept.
+bool carve_scratch(void* base, uint64_t bytes, uint64_t n, Scratch* out) {
+  int bits = 10;
+  while ((1ull << bits) < 2 * n) ++bits;
+  const uint64_t T = 1ull << bits;
+  const uint64_t sz_tab = align256(T * sizeof(DedupEntry));
+  const uint64_t sz_ts = align256(T);
+  const uint64_t sz_u8 = align256(n);
+  const uint64_t sz_u32 = align256(n * 4);
+  const uint64_t sz_u64 = align256(n * 8);
+  const uint64_t sz_cnt = align256(kCntWords * 8);
+  const uint64_t total = sz_tab + sz_ts + 4 * sz_u32 + sz_cnt + sz_u8 + 3 * sz_u64;
+  if (total > bytes) return false;
+  char* p = static_cast<char*>(base);
+  Scratch s{};
+  s.tab = reinterpret_cast<DedupEntry*>(p); p += sz_tab;
+  s.tab_bits = bits;
+  s.tab_mask = T - 1;
+  s.tstatus = reinterpret_cast<uint8_t*>(p); p += sz_ts;
+  s.slot_of = reinterpret_cast<uint32_t*>(p); p += sz_u32;
+  s.ulist = reinterpret_cast<uint32_t*>(p); p += sz_u32;
+  s.cnt = reinterpret_cast<unsigned long long*>(p); p += sz_cnt;
+  s.mflag = reinterpret_cast<uint8_t*>(p); p += sz_u8;
+  s.mkey = reinterpret_cast<uint64_t*>(p); p += sz_u64;
+  s.evk = reinterpret_cast<uint64_t*>(p); p += sz_u64;
+  s.evs = reinterpret_cast<uint64_t*>(p); p += sz_u64;
+  s.mi = reinterpret_cast<uint32_t*>(p); p += sz_u32;
+  s.mm = reinterpret_cast<uint32_t*>(p); p += sz_u32;
+  s.evv = nullptr;
+  *out = s;
+  return true;
+}
+
+}  // namespace
+
+hkv_status launch_upsert_in(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,
+                            const uint64_t* scores, uint8_t* status_out, uint64_t* ev_keys,
+                            uint64_t* ev_scores, uint64_t* n_evicted, ScoreCtx ctx,
+                            void* scratch, uint64_t scratch_bytes, cudaStream_t st) {
+  if (n == 0) {
+    if (n_evicted) cudaMemsetAsync(n_evicted, 0, 8, st);
+    return cuda_status(cudaGetLastError(), "upsert");
+  }
+  Scratch s;
+  if (!carve_scratch(scratch, scratch_bytes, n, &s)) {
+    set_last_error("batch too large for the scratch block");
+    return HKV_ERR_INVALID_ARG;
+  }
+  // The block keeps the previous call's contents: reset what must start
+  // empty or zero.
+  cudaMemsetAsync(s.tab, 0xFF, (s.tab_mask + 1) * sizeof(DedupEntry), st);
+  cudaMemsetAsync(s.cnt, 0, kCntWords * 8, st);
+  const bool vec16 = t->dev.dim % 4 == 0 && aligned16(values);
+  launch_dedup(t, n, keys, s, st);
+  launch_update<true>(t, n, s, values, scores, ctx, vec16, st);
+  {
+    const unsigned ig = grid_for(t, (n + 31) / 32 * 32, kInsThreads, 4);
+    KernelTimer timer(t->prof, HKV_K_INSERT, st);
+    if (vec16)
+      insert_kernel<true><<<ig, kInsThreads, 0, st>>>(t->dev, s, values, scores, ctx);
+    else
+      insert_kernel<false><<<ig, kInsThreads, 0, st>>>(t->dev, s, values, scores, ctx);
+  }
+  {
+    KernelTimer timer(t->prof, HKV_K_RECONCILE, st);
+    reconcile_kernel<<<grid_for(t, n, kRecThreads, 8), kRecThreads, 0, st>>>(
+        t->dev, s, ev_keys, ev_scores, nullptr);
+  }
+  if (status_out || n_evicted) {
+    KernelTimer timer(t->prof, HKV_K_STATUS, st);
+    status_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(n, s, status_out, n_evicted);
+  }
+  return cuda_status(cudaGetLastError(), "insert_or_assign launch");
+}
+
+}  // namespace hkv
