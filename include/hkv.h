@@ -241,6 +241,39 @@ hkv_status hkv_reset_counters(hkv_table_t t, hkv_stream_t stream);
  * these; defaults follow the value width. */
 hkv_status hkv_set_launch(hkv_table_t t, int find_threads_per_key, int update_threads_per_key);
 
+/* Batched multi-table rounds (the paper has no batched multi-table API;
+ * this is the library's serving-side addition). A batch object binds
+ * n_slots distinct tables, each with the largest number of keys a round
+ * may give it (max_keys[i] < 2^31), and owns their per-round scratch.
+ * hkv_batch_run executes one round: ops[i] (HKV_OP_NONE, HKV_OP_FIND or
+ * HKV_OP_UPSERT) on slot i's table, all slots side by side. With use_graph
+ * the round is one launch of a CUDA graph captured once per combination of
+ * operations and launch shapes; without, the same kernels are launched
+ * directly on one stream per slot. Either way the round's sizes and buffer
+ * pointers travel in a small descriptor copied to the device at the start
+ * of the round, the caller's stream waits for every slot, and each table
+ * takes its triple-group role (find: reader, upsert: inserter) for the
+ * round. Results are those of hkv_find / hkv_insert_or_assign with
+ * found[] / status_out[] in ops[i].flags (nullable for upserts); upsert
+ * evictions are not reported. Value rows must be 16-byte aligned.
+ * Asynchronous on `stream`; the op array is read before the call returns. */
+typedef struct hkv_batch_s *hkv_batch_t;
+enum { HKV_OP_NONE = 0, HKV_OP_FIND = 1, HKV_OP_UPSERT = 2 };
+typedef struct {
+  int32_t op;               /* HKV_OP_* */
+  uint64_t n;               /* keys this round, <= the slot's max_keys */
+  const uint64_t *keys;     /* device [n] */
+  const float *values_in;   /* upsert: device [n][dim] */
+  float *values_out;        /* find: device [n][dim] */
+  uint8_t *flags;           /* find: found[n]; upsert: status[n] or NULL */
+  const uint64_t *scores;   /* upsert under HKV_CUSTOM: device [n]; else NULL */
+} hkv_batch_op;
+hkv_status hkv_batch_create(int n_slots, const hkv_table_t *tables, const uint64_t *max_keys,
+                            hkv_batch_t *out);
+hkv_status hkv_batch_run(hkv_batch_t b, const hkv_batch_op *ops, int use_graph,
+                         hkv_stream_t stream);
+hkv_status hkv_batch_destroy(hkv_batch_t b);
+
 /* Measurement hook. While enabled, every kernel the library launches for
  * this table is bracketed by two CUDA events recorded on the launching
  * stream. hkv_profile_read waits for those events and returns, per kernel

@@ -38,6 +38,13 @@ class Options(ctypes.Structure):
                 ("deterministic", _i32), ("hbm_value_budget_bytes", _u64), ("slice_bytes", _u64)]
 
 
+class BatchOp(ctypes.Structure):
+    _fields_ = [("op", _i32), ("n", _u64), ("keys", _vp), ("values_in", _vp),
+                ("values_out", _vp), ("flags", _vp), ("scores", _vp)]
+
+
+OP_NONE, OP_FIND, OP_UPSERT = 0, 1, 2
+
 SIGNATURES = {
     "hkv_create": (_i32, [ctypes.POINTER(Options), ctypes.POINTER(_vp)]),
     "hkv_destroy": (_i32, [_vp]),
@@ -60,6 +67,9 @@ SIGNATURES = {
     "hkv_read_counters": (_i32, [_vp, _P64, _vp]),
     "hkv_reset_counters": (_i32, [_vp, _vp]),
     "hkv_set_launch": (_i32, [_vp, _i32, _i32]),
+    "hkv_batch_create": (_i32, [_i32, ctypes.POINTER(_vp), _P64, ctypes.POINTER(_vp)]),
+    "hkv_batch_run": (_i32, [_vp, ctypes.POINTER(BatchOp), _i32, _vp]),
+    "hkv_batch_destroy": (_i32, [_vp]),
     "hkv_profile_enable": (_i32, [_vp, _i32]),
     "hkv_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), _P64]),
     "hkv_last_error": (ctypes.c_char_p, []),
@@ -293,3 +303,83 @@ class Table:
     def set_launch(self, find_threads_per_key: int = 0, update_threads_per_key: int = 0):
         _check(load_library().hkv_set_launch(self._h, find_threads_per_key,
                                              update_threads_per_key))
+
+
+class Batch:
+    """Batched multi-table rounds over a fixed set of tables (one slot each;
+    see hkv_batch_run in include/hkv.h)."""
+
+    def __init__(self, tables, max_keys):
+        L = load_library()
+        self.tables = list(tables)
+        n = len(self.tables)
+        arr = (_vp * n)(*[t.handle.value for t in self.tables])
+        mk = (ctypes.c_uint64 * n)(*[int(m) for m in max_keys])
+        h = ctypes.c_void_p()
+        _check(L.hkv_batch_create(n, arr, mk, ctypes.byref(h)))
+        self._h = h
+        self.max_keys = list(max_keys)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(load_library().hkv_batch_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def make_ops(self, ops):
+        """Pack a round's ops (see run) into the C array hkv_batch_run reads."""
+        n = len(self.tables)
+        arr = (BatchOp * n)()
+        for i, o in enumerate(ops):
+            if o is None:
+                arr[i].op = OP_NONE
+                continue
+            keys = o["keys"]
+            arr[i].op = o["op"]
+            arr[i].n = int(o.get("n", keys.numel()))
+            arr[i].keys = keys.data_ptr()
+            vals = o.get("values")
+            if o["op"] == OP_FIND:
+                arr[i].values_out = vals.data_ptr()
+            else:
+                arr[i].values_in = vals.data_ptr()
+            fl = o.get("flags")
+            arr[i].flags = fl.data_ptr() if fl is not None else None
+            sc = o.get("scores")
+            arr[i].scores = sc.data_ptr() if sc is not None else None
+        return arr
+
+    def run_packed(self, arr, use_graph=True, stream=None):
+        _check(load_library().hkv_batch_run(self._h, arr, int(use_graph), _stream(stream)))
+
+    def run(self, ops, use_graph=True, stream=None):
+        """ops: one entry per slot, None or a dict with keys op (OP_FIND /
+        OP_UPSERT), keys, values (find: output rows; upsert: input rows),
+        flags (found / status, optional for upsert), scores (optional), n
+        (default keys.numel())."""
+        n = len(self.tables)
+        arr = (BatchOp * n)()
+        for i, o in enumerate(ops):
+            if o is None:
+                arr[i].op = OP_NONE
+                continue
+            keys = o["keys"]
+            cnt = int(o.get("n", keys.numel()))
+            arr[i].op = o["op"]
+            arr[i].n = cnt
+            arr[i].keys = keys.data_ptr()
+            vals = o.get("values")
+            if o["op"] == OP_FIND:
+                arr[i].values_out = vals.data_ptr()
+            else:
+                arr[i].values_in = vals.data_ptr()
+            fl = o.get("flags")
+            arr[i].flags = fl.data_ptr() if fl is not None else None
+            sc = o.get("scores")
+            arr[i].scores = sc.data_ptr() if sc is not None else None
+        _check(load_library().hkv_batch_run(self._h, arr, int(use_graph), _stream(stream)))

@@ -43,6 +43,28 @@ struct ScoreCtx {
   uint64_t epoch;
 };
 
+// One table's work in a batched round, kept in device memory so that a
+// captured launch sequence can be replayed with new sizes and buffers: the
+// kernels read their size, pointers and score context from here when given
+// one.
+struct OpDesc {
+  uint64_t n;
+  const uint64_t* keys;
+  const float* values_in;   // upsert input rows
+  float* values_out;        // find output rows
+  uint8_t* flags;           // find: found; upsert: status (may be null)
+  const uint64_t* scores;   // caller scores (HKV_CUSTOM), else null
+  uint64_t step;
+  uint64_t epoch;
+};
+
+// log2 of the dedup table size for a batch of n keys (>= 2n, >= 1024).
+__host__ __device__ __forceinline__ int tab_bits_for(uint64_t n) {
+  int b = 10;
+  while ((1ull << b) < 2 * n) ++b;
+  return b;
+}
+
 // ------------------------------------------------------------------ hashing
 
 // MurmurHash3 64-bit finaliser (public-domain construction): the table's

@@ -19,7 +19,13 @@ template <int G, bool VEC16, bool VALUES>
 __global__ void __launch_bounds__(kFindThreads)
     find_kernel(TableDev t, uint64_t n, const uint64_t* __restrict__ keys,
                 float* __restrict__ out, uint8_t* __restrict__ found,
-                uint64_t* __restrict__ scores_out) {
+                uint64_t* __restrict__ scores_out, const OpDesc* __restrict__ d) {
+  if (d) {
+    n = d->n;
+    keys = d->keys;
+    out = d->values_out;
+    found = d->flags;
+  }
   constexpr int KPW = 32 / G;
   const int lane = threadIdx.x & 31;
   const int lane_g = lane & (G - 1);
@@ -72,21 +78,23 @@ __global__ void __launch_bounds__(kFindThreads)
 
 template <int G>
 void launch_g(const hkv_table_s* t, uint64_t n, const uint64_t* keys, float* out, uint8_t* found,
-              uint64_t* scores_out, bool vec16, cudaStream_t s) {
+              uint64_t* scores_out, bool vec16, cudaStream_t s, const OpDesc* d = nullptr,
+              bool values_if_desc = false) {
+  const bool values = d ? values_if_desc : out != nullptr;
   uint64_t warps_needed = (n + (32 / G) - 1) / (32 / G);
   uint64_t blocks = (warps_needed * 32 + kFindThreads - 1) / kFindThreads;
   uint64_t cap = (uint64_t)t->num_sms * (2048 / kFindThreads);
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
-  if (!out)
+  if (!values)
     find_kernel<G, false, false><<<(unsigned)blocks, kFindThreads, 0, s>>>(t->dev, n, keys, out,
-                                                                           found, scores_out);
+                                                                           found, scores_out, d);
   else if (vec16)
     find_kernel<G, true, true><<<(unsigned)blocks, kFindThreads, 0, s>>>(t->dev, n, keys, out,
-                                                                         found, scores_out);
+                                                                         found, scores_out, d);
   else
     find_kernel<G, false, true><<<(unsigned)blocks, kFindThreads, 0, s>>>(t->dev, n, keys, out,
-                                                                          found, scores_out);
+                                                                          found, scores_out, d);
 }
 
 }  // namespace
@@ -105,6 +113,23 @@ hkv_status launch_find(hkv_table_s* t, uint64_t n, const uint64_t* keys, float* 
     default: launch_g<8>(t, n, keys, values_out, found, scores_out, vec16, s); break;
   }
   return cuda_status(cudaGetLastError(), "find launch");
+}
+
+hkv_status launch_find_desc(hkv_table_s* t, uint64_t n_max, const OpDesc* d, bool values,
+                            cudaStream_t s) {
+  // Sized for n_max; the kernel reads the round's size and buffers from d,
+  // whose value rows the batch object keeps 16-byte aligned.
+  const uint64_t n = n_max ? n_max : 1;
+  const bool vec16 = t->dev.dim % 4 == 0;
+  switch (t->launch.find_tpk) {
+    case 1: launch_g<1>(t, n, nullptr, nullptr, nullptr, nullptr, vec16, s, d, values); break;
+    case 2: launch_g<2>(t, n, nullptr, nullptr, nullptr, nullptr, vec16, s, d, values); break;
+    case 4: launch_g<4>(t, n, nullptr, nullptr, nullptr, nullptr, vec16, s, d, values); break;
+    case 16: launch_g<16>(t, n, nullptr, nullptr, nullptr, nullptr, vec16, s, d, values); break;
+    case 32: launch_g<32>(t, n, nullptr, nullptr, nullptr, nullptr, vec16, s, d, values); break;
+    default: launch_g<8>(t, n, nullptr, nullptr, nullptr, nullptr, vec16, s, d, values); break;
+  }
+  return cuda_status(cudaGetLastError(), "batched find launch");
 }
 
 }  // namespace hkv

@@ -139,6 +139,14 @@ hkv_status launch_upsert_in(hkv_table_s* t, uint64_t n, const uint64_t* keys, co
                             const uint64_t* scores, uint8_t* status_out, uint64_t* ev_keys,
                             uint64_t* ev_scores, uint64_t* n_evicted, ScoreCtx ctx,
                             void* scratch, uint64_t scratch_bytes, cudaStream_t s);
+// Batched rounds: size, buffers and score context come from a device
+// OpDesc; grids are sized for n_max, scratch is the caller's block of
+// upsert_scratch_bytes(n_max) bytes. No allocation, no profiling events.
+uint64_t upsert_scratch_bytes(uint64_t n_max);
+hkv_status launch_find_desc(hkv_table_s* t, uint64_t n_max, const OpDesc* d, bool values,
+                            cudaStream_t s);
+hkv_status launch_upsert_desc(hkv_table_s* t, uint64_t n_max, const OpDesc* d, void* scratch,
+                              uint64_t scratch_bytes, cudaStream_t s);
 hkv_status launch_assign(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,
                          const uint64_t* scores, ScoreCtx ctx, cudaStream_t s);
 hkv_status launch_erase(hkv_table_s* t, uint64_t n, const uint64_t* keys, cudaStream_t s);

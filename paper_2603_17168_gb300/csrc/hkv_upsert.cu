@@ -64,6 +64,7 @@ struct Scratch {
   uint64_t* evk;             // [n] victim of distinct key u, kEmptyKey if none
   uint64_t* evs;             // [n] its score
   float* evv;                // [n][dim] its value, or null
+  const OpDesc* d;           // batched rounds: size, buffers and score context
 };
 
 __device__ __forceinline__ uint64_t dedup_pos(uint64_t key, int bits) {
@@ -95,6 +96,15 @@ __global__ void __launch_bounds__(kDedupThreads)
                  int deterministic) {
   extern __shared__ DedupEntry sm[];
   constexpr uint32_t kMask = kDedupEntries - 1;
+  int tab_bits = s.tab_bits;
+  uint64_t tab_mask = s.tab_mask;
+  if (s.d) {  // grid sized for the batch object's largest round
+    n = s.d->n;
+    keys = s.d->keys;
+    tab_bits = tab_bits_for(n);
+    tab_mask = (1ull << tab_bits) - 1;
+    if ((uint64_t)blockIdx.x * kDedupTile >= n) return;
+  }
   for (int p = threadIdx.x; p < kDedupEntries; p += kDedupThreads) {
     sm[p].key = kEmptyKey;
     sm[p].nlast = 0xFFFFFFFFu;
@@ -134,13 +144,13 @@ __global__ void __launch_bounds__(kDedupThreads)
     const unsigned long long k = sm[p].key;
     if (k == kEmptyKey) continue;
     const uint32_t c = sm[p].cnt_m1 + 1u;
-    uint64_t gp = dedup_pos(k, s.tab_bits);
+    uint64_t gp = dedup_pos(k, tab_bits);
     bool first = false;
     for (;;) {  // the table holds >= 2n entries: terminates
       const unsigned long long old = atomicCAS(&s.tab[gp].key, kEmptyKey, k);
       if (old == kEmptyKey) { first = true; break; }
       if (old == k) break;
-      gp = (gp + 1) & s.tab_mask;
+      gp = (gp + 1) & tab_mask;
     }
     atomicMin(&s.tab[gp].nlast, sm[p].nlast);
     atomicAdd(&s.tab[gp].cnt_m1, c);
@@ -178,6 +188,12 @@ __global__ void __launch_bounds__(kUpdThreads)
     update_kernel(TableDev t, Scratch s, const float* __restrict__ values,
                   const uint64_t* __restrict__ scores_in, ScoreCtx ctx) {
   if (aborted(s)) return;
+  if (s.d) {
+    values = s.d->values_in;
+    scores_in = s.d->scores;
+    ctx.step = s.d->step;
+    ctx.epoch = s.d->epoch;
+  }
   constexpr int KPW = 32 / G;
   const int lane = threadIdx.x & 31;
   const int lane_g = lane & (G - 1);
@@ -338,6 +354,12 @@ __global__ void __launch_bounds__(kInsThreads, 4)
     insert_kernel(TableDev t, Scratch s, const float* __restrict__ values,
                   const uint64_t* __restrict__ scores_in, ScoreCtx ctx) {
   if (aborted(s)) return;
+  if (s.d) {
+    values = s.d->values_in;
+    scores_in = s.d->scores;
+    ctx.step = s.d->step;
+    ctx.epoch = s.d->epoch;
+  }
   const int lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * (uint64_t)kInsThreads + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * kInsThreads) >> 5;
@@ -561,6 +583,8 @@ __global__ void __launch_bounds__(kRecThreads)
     reconcile_kernel(TableDev t, Scratch s, uint64_t* __restrict__ ev_keys,
                      uint64_t* __restrict__ ev_scores, float* __restrict__ ev_values) {
   if (aborted(s)) return;
+  const int tab_bits = s.d ? tab_bits_for(s.d->n) : s.tab_bits;
+  const uint64_t tab_mask = (1ull << tab_bits) - 1;
   const uint64_t nu = s.cnt[kCntUnique];
   for (uint64_t base = (uint64_t)blockIdx.x * kRecThreads; base < nu;
        base += (uint64_t)gridDim.x * kRecThreads) {
@@ -569,7 +593,7 @@ __global__ void __launch_bounds__(kRecThreads)
     if (u < nu && s.mflag[u]) k = s.evk[u];
     bool out = k != kEmptyKey;
     if (out) {
-      uint64_t gp = dedup_pos(k, s.tab_bits);
+      uint64_t gp = dedup_pos(k, tab_bits);
       for (;;) {
         const uint64_t tk = s.tab[gp].key;
         if (tk == k) {
@@ -581,7 +605,7 @@ __global__ void __launch_bounds__(kRecThreads)
           break;
         }
         if (tk == kEmptyKey) break;
-        gp = (gp + 1) & s.tab_mask;
+        gp = (gp + 1) & tab_mask;
       }
     }
     const unsigned long long o = block_reserve(s.cnt + kCntEvOut, out ? 1u : 0u);
@@ -597,6 +621,10 @@ __global__ void __launch_bounds__(kRecThreads)
 __global__ void status_kernel(uint64_t n, Scratch s, uint8_t* __restrict__ status_out,
                               uint64_t* __restrict__ n_evicted) {
   if (aborted(s)) return;
+  if (s.d) {
+    n = s.d->n;
+    status_out = s.d->flags;
+  }
   if (status_out)
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x)
@@ -900,6 +928,55 @@ hkv_status launch_upsert_in(hkv_table_s* t, uint64_t n, const uint64_t* keys, co
     status_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(n, s, status_out, n_evicted);
   }
   return cuda_status(cudaGetLastError(), "insert_or_assign launch");
+}
+
+}  // namespace hkv
+
+// ------------------------------------------------ batched rounds (OpDesc)
+
+namespace hkv {
+namespace {
+
+// Reset the dedup table entries a round of d->n keys uses, and the counters.
+__global__ void clear_kernel(Scratch s) {
+  const uint64_t T = 1ull << tab_bits_for(s.d->n);
+  uint4* p = reinterpret_cast<uint4*>(s.tab);
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < T;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    p[i] = make_uint4(~0u, ~0u, ~0u, ~0u);
+  if (blockIdx.x == 0 && threadIdx.x < kCntWords) s.cnt[threadIdx.x] = 0;
+}
+
+}  // namespace
+
+uint64_t upsert_scratch_bytes(uint64_t n) {
+  const uint64_t T = 1ull << tab_bits_for(n);
+  return align256(T * sizeof(DedupEntry)) + align256(T) + 4 * align256(n * 4) +
+         align256(kCntWords * 8) + align256(n) + 3 * align256(n * 8);
+}
+
+hkv_status launch_upsert_desc(hkv_table_s* t, uint64_t n_max, const OpDesc* d, void* scratch,
+                              uint64_t scratch_bytes, cudaStream_t st) {
+  Scratch s;
+  const uint64_t n = n_max ? n_max : 1;
+  if (!carve_scratch(scratch, scratch_bytes, n, &s)) {
+    set_last_error("batch slot scratch too small");
+    return HKV_ERR_INVALID_ARG;
+  }
+  s.d = d;
+  const bool vec16 = t->dev.dim % 4 == 0;
+  clear_kernel<<<grid_for(t, s.tab_mask + 1, 256, 8), 256, 0, st>>>(s);
+  launch_dedup(t, n, nullptr, s, st);
+  launch_update<true>(t, n, s, nullptr, nullptr, ScoreCtx{0, 0}, vec16, st);
+  const unsigned ig = grid_for(t, (n + 31) / 32 * 32, kInsThreads, 4);
+  if (vec16)
+    insert_kernel<true><<<ig, kInsThreads, 0, st>>>(t->dev, s, nullptr, nullptr, ScoreCtx{0, 0});
+  else
+    insert_kernel<false><<<ig, kInsThreads, 0, st>>>(t->dev, s, nullptr, nullptr, ScoreCtx{0, 0});
+  reconcile_kernel<<<grid_for(t, n, kRecThreads, 8), kRecThreads, 0, st>>>(t->dev, s, nullptr,
+                                                                             nullptr, nullptr);
+  status_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(n, s, nullptr, nullptr);
+  return cuda_status(cudaGetLastError(), "batched upsert launch");
 }
 
 }  // namespace hkv
