@@ -58,6 +58,10 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--find-tpk", type=int, default=0)
     p.add_argument("--update-tpk", type=int, default=0)
+    p.add_argument("--workload", choices=("single", "multi"), default="single")
+    p.add_argument("--multi-lambda", type=float, default=1.0)
+    p.add_argument("--multi-shrink", type=int, default=0,
+                   help="divide the multi-table slot counts by 2^k (small runs)")
     p.add_argument("--lambdas", type=str, default=",".join(str(x) for x in LAMBDAS),
                    help="comma-separated load factors (a subset, for profiling runs)")
     a = p.parse_args(argv)
@@ -546,10 +550,136 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
 
 
+# ----------------------------------------------------- multi-table workload
+
+MULTI_WORKLOAD = ("8 tables of 2^22-2^25 slots, dims {16, 32, 64, 64, 128, 128, 256, 8} fp32, LRU, "
+                  "single-bucket, pre-filled with uniform keys; per round and table a batch of "
+                  "lognormal size (median 32K, sigma 1, clipped to 1K-512K) of Zipf(1.05) keys "
+                  "over 2^32, find w.p. 0.8 else insert_or_assign")
+
+
+def run_multi(args):
+    """Batched multi-table rounds vs plain per-table calls on the same rounds."""
+    import ctypes
+
+    import torch
+    import paper_2603_17168_gb300 as hkv
+    from paper_2603_17168_gb300 import autotune
+    from paper_2603_17168_gb300 import workloads as w
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(w.seed_for(3, rank))
+    rng = np.random.default_rng(w.seed_for(3, 100 + rank))
+    maxn, pools = 524288, 3
+    shrink = args.multi_shrink
+    tables = []
+    for slots, dim in zip(w.MULTI_SLOTS, w.MULTI_DIMS):
+        t = hkv.Table(slots >> shrink, dim, hkv.LRU)
+        fill_table(t, args.multi_lambda, gen, dim)
+        tables.append(t)
+    z = w.Zipf(ALPHA, UNIVERSE)
+    pk = [[w.zipf_keys_torch(gen, z, maxn) for _ in range(pools)] for _ in tables]
+    pv = [[torch.randn((maxn, t.dim), device=dev, generator=gen) for _ in range(pools)]
+          for t in tables]
+    outs = [torch.empty((maxn, t.dim), device=dev) for t in tables]
+    flags = [torch.empty(maxn, dtype=torch.uint8, device=dev) for _ in tables]
+    tuned = {}
+    for i, t in enumerate(tables):
+        c = autotune.tune(t, pk[i][0][:32768].contiguous())
+        tuned[f"dim{t.dim}_slot{i}"] = {"find_tpk": c["find_tpk"], "update_tpk": c["update_tpk"]}
+    batch = hkv.Batch(tables, [maxn] * len(tables))
+    L = hkv.load_library()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    nround = args.warmup + args.steps
+    rounds = []
+    for r in range(nround):
+        ops = []
+        for i, t in enumerate(tables):
+            n = int(np.clip(np.rint(np.exp(np.log(32768) + rng.standard_normal())), 1024, maxn))
+            op = hkv.OP_FIND if rng.random() < 0.8 else hkv.OP_UPSERT
+            p = r % pools
+            off = int(rng.integers(0, maxn - n + 1))
+            keys = pk[i][p][off:off + n]
+            vals = outs[i][:n] if op == hkv.OP_FIND else pv[i][p][off:off + n]
+            ops.append(dict(op=op, keys=keys, values=vals, flags=flags[i][:n], n=n))
+        rounds.append(ops)
+    keys_timed = sum(o["n"] for ops in rounds[args.warmup:] for o in ops)
+    packed = [batch.make_ops(ops) for ops in rounds]
+    plain_args = []
+    for ops in rounds:
+        calls = []
+        for t, o in zip(tables, ops):
+            kp, vp, fp = (ctypes.c_void_p(o["keys"].data_ptr()), ctypes.c_void_p(o["values"].data_ptr()),
+                          ctypes.c_void_p(o["flags"].data_ptr()))
+            if o["op"] == hkv.OP_FIND:
+                calls.append((L.hkv_find, (t.handle, o["n"], kp, vp, fp, None, stream)))
+            else:
+                calls.append((L.hkv_insert_or_assign,
+                              (t.handle, o["n"], kp, vp, None, fp, None, None, None, None, stream)))
+        plain_args.append(calls)
+
+    def plain(r):
+        for fn, a in plain_args[r]:
+            fn(*a)
+
+    def graph(r):
+        batch.run_packed(packed[r], True)
+
+    def direct(r):
+        batch.run_packed(packed[r], False)
+
+    res = {}
+    for name, fn in (("plain", plain), ("graph", graph), ("multistream", direct)):
+        for r in range(args.warmup):
+            fn(r)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0 = time.perf_counter()
+        e0.record()
+        for r in range(args.warmup, nround):
+            fn(r)
+        e1.record()
+        host_ms = (time.perf_counter() - h0) * 1e3
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        ms, units = reduce_max_sum(ms, float(keys_timed), world, dev)
+        res[name] = {"bkvs": round(units / (ms * 1e-3) / 1e9, 4),
+                     "ms_per_round": round(ms / args.steps, 4),
+                     "host_issue_ms_per_round": round(host_ms / args.steps, 4)}
+    for t in tables:
+        t.sync()
+    batch.close()
+    out = None
+    if rank == 0:
+        out = {"metric": METRIC, "value": res["graph"]["bkvs"], "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": res["graph"]["ms_per_round"], "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+               "config": {"workload": MULTI_WORKLOAD, "lambda": args.multi_lambda,
+                          "slots_shift": shrink, "rounds_timed": args.steps,
+                          "keys_per_round_mean": round(keys_timed / args.steps),
+                          "step": "one round: 8 tables, one operation each"},
+               "paths": res, "speedup_graph_vs_plain": round(res["graph"]["bkvs"] / res["plain"]["bkvs"], 3),
+               "autotune": tuned}
+    for t in tables:
+        t.close()
+    return out
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         res = run_reference(args)
+    elif args.workload == "multi":
+        import __graft_entry__ as g
+        g.build()
+        res = run_multi(args)
     else:
         import __graft_entry__ as g
         g.build()
