@@ -58,7 +58,11 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--find-tpk", type=int, default=0)
     p.add_argument("--update-tpk", type=int, default=0)
-    p.add_argument("--workload", choices=("single", "multi"), default="single")
+    p.add_argument("--workload", choices=("single", "multi", "serve"), default="single")
+    p.add_argument("--serve-budget-gib", type=float, default=120.0)
+    p.add_argument("--serve-pool", type=int, default=512)
+    p.add_argument("--serve-peak-requests", type=int, default=4096)
+    p.add_argument("--serve-seconds", type=float, default=3.0)
     p.add_argument("--multi-lambda", type=float, default=1.0)
     p.add_argument("--multi-shrink", type=int, default=0,
                    help="divide the multi-table slot counts by 2^k (small runs)")
@@ -672,6 +676,106 @@ def run_multi(args):
     return out
 
 
+# ----------------------------------------------------------- serving loop
+
+SERVE_WORKLOAD = ("serving: the 8 multi-table tables (LRU, pre-filled to lambda 1.0) behind the "
+                  "continuous-batching loop; requests find (0.8) / insert_or_assign (0.2), "
+                  "lognormal sizes (median 4096, sigma 1.5, clipped to 256-262144) of Zipf(1.1) "
+                  "keys over 2^32 on a uniformly chosen table, Poisson arrivals; inputs from and "
+                  "results to pinned host memory")
+
+
+def _latency_stats(items, res):
+    lat = np.array([(r.done_s - it["arrival_s"]) * 1e3 for r, it in zip(res, items)])
+    span = max(r.done_s for r in res) - min(it["arrival_s"] for it in items)
+    keys = sum(int(it["keys"].numel()) for it in items)
+    return {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "bkvs": round(keys / span / 1e9, 4), "requests": len(items),
+            "rounds": len({r.round for r in res})}
+
+
+def run_serve(args):
+    import torch
+    import paper_2603_17168_gb300 as hkv
+    from paper_2603_17168_gb300 import autotune
+    from paper_2603_17168_gb300 import workloads as w
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(w.seed_for(5, rank))
+    rng = np.random.default_rng(w.seed_for(5, 100 + rank))
+    shrink = args.multi_shrink
+    tables = []
+    for slots, dim in zip(w.MULTI_SLOTS, w.MULTI_DIMS):
+        t = hkv.Table(slots >> shrink, dim, hkv.LRU)
+        fill_table(t, 1.0, gen, dim)
+        autotune.tune(t, w.zipf_keys_torch(gen, w.Zipf(1.1, UNIVERSE), 4096))
+        tables.append(t)
+    budget = int(args.serve_budget_gib * (1 << 30))
+    srv = hkv.Server(tables, ring_keys=1 << 20, hbm_budget_bytes=budget, max_inflight=3)
+    server_gib = srv.hbm_bytes / (1 << 30)
+    z = w.Zipf(1.1, UNIVERSE)
+    pool = []
+    for _ in range(args.serve_pool):
+        tab = int(rng.integers(0, len(tables)))
+        n = int(np.clip(np.rint(np.exp(np.log(4096) + 1.5 * rng.standard_normal())), 256, 262144))
+        op = hkv.OP_FIND if rng.random() < 0.8 else hkv.OP_UPSERT
+        dim = tables[tab].dim
+        keys = torch.from_numpy(z.keys(rng, n).view(np.int64)).pin_memory()
+        vals = (torch.empty((n, dim), dtype=torch.float32).pin_memory() if op == hkv.OP_FIND else
+                torch.from_numpy(w.normal_values(rng, n, dim)).pin_memory())
+        flags = torch.empty(n, dtype=torch.uint8).pin_memory()
+        pool.append(dict(table=tab, op=op, keys=keys, values=vals, flags=flags))
+    mean_n = float(np.mean([p["keys"].numel() for p in pool]))
+
+    def make(n_req, rate):
+        items, t = [], 0.0
+        for i in range(n_req):
+            if rate:
+                t += rng.exponential(1.0 / rate)
+            it = dict(pool[i % len(pool)])
+            it["arrival_s"] = t
+            items.append(it)
+        return items
+
+    # warm the graphs and the pipeline
+    warm = make(min(256, len(pool)), 0)
+    srv.run(hkv.make_requests(warm), batched=True)
+    srv.run(hkv.make_requests(warm[:64]), batched=False)
+    # peak: closed loop, every request queued at t = 0
+    peak_items = make(args.serve_peak_requests, 0)
+    peak_b = _latency_stats(peak_items, srv.run(hkv.make_requests(peak_items), batched=True))
+    peak_p = _latency_stats(peak_items, srv.run(hkv.make_requests(peak_items), batched=False))
+    peak_keys_s = peak_b["bkvs"] * 1e9
+    served = {}
+    for frac in (0.25, 0.50, 0.90):
+        rate = frac * peak_keys_s / mean_n
+        n_req = max(64, int(rate * args.serve_seconds))
+        items = make(n_req, rate)
+        reqs = hkv.make_requests(items)
+        served[f"{int(frac * 100)}%"] = {
+            "offered_bkvs": round(frac * peak_keys_s / 1e9, 4),
+            "batched": _latency_stats(items, srv.run(reqs, batched=True)),
+            "plain": _latency_stats(items, srv.run(reqs, batched=False))}
+    srv.close()
+    for t in tables:
+        t.close()
+    return {"metric": METRIC, "value": peak_b["bkvs"], "unit": UNIT, "n_gpus": world,
+            "steps": args.serve_peak_requests, "warmup": 1, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": SERVE_WORKLOAD, "slots_shift": shrink,
+                       "hbm_budget_gib": args.serve_budget_gib,
+                       "server_hbm_gib": round(server_gib, 2),
+                       "ring_keys_per_table": 1 << 20, "max_inflight_rounds": 3,
+                       "request_pool": len(pool), "mean_request_keys": round(mean_n),
+                       "seconds_per_load": args.serve_seconds,
+                       "step": "a request; value = closed-loop peak of the batched loop"},
+            "peak": {"batched": peak_b, "plain": peak_p}, "served": served}
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -680,6 +784,10 @@ def main(argv=None):
         import __graft_entry__ as g
         g.build()
         res = run_multi(args)
+    elif args.workload == "serve":
+        import __graft_entry__ as g
+        g.build()
+        res = run_serve(args)
     else:
         import __graft_entry__ as g
         g.build()

@@ -274,6 +274,50 @@ hkv_status hkv_batch_run(hkv_batch_t b, const hkv_batch_op *ops, int use_graph,
                          hkv_stream_t stream);
 hkv_status hkv_batch_destroy(hkv_batch_t b);
 
+/* Serving loop with continuous batching (the paper has no serving layer;
+ * this is the library's addition). A server binds n_tables device-resident
+ * tables (not HKV_CUSTOM) and gives each a staging ring of ring_keys keys in
+ * HBM. hkv_serve_create refuses with HKV_ERR_OOM when the tables plus the
+ * staging exceed hbm_budget_bytes (0: no budget).
+ * hkv_serve_run replays a trace of requests in real time: a request is
+ * admitted when its keys fit in its table's ring (its inputs are then copied
+ * in on a copy stream); while fewer than max_inflight rounds are on the GPU,
+ * a round takes, for every table with admitted work, the head of that
+ * table's FIFO merged with the following finds that sit next to it in the
+ * ring (an upsert always runs alone), runs them as one batched multi-table
+ * launch (hkv_batch_run, with use_graph), copies each request's results
+ * back to its host buffers and records a completion event. Every request
+ * therefore sees its table exactly as it would alone, in arrival order.
+ * With batched = 0 the same trace runs one request at a time through
+ * hkv_find / hkv_insert_or_assign, oldest first (the plain path).
+ * Synchronous: returns when every request has completed; results[i] gets
+ * the admission and completion times (seconds since the run started,
+ * host clock, completion stamped by polling the round's event) and the
+ * round that carried it. Find rows of misses are left unspecified. */
+typedef struct hkv_server_s *hkv_server_t;
+typedef struct {
+  double arrival_s;        /* seconds from the start of the run; non-decreasing */
+  int32_t table;           /* index into the server's tables */
+  int32_t op;              /* HKV_OP_FIND or HKV_OP_UPSERT */
+  uint64_t n;              /* 1..ring_keys */
+  const uint64_t *keys;    /* pinned host [n] */
+  const float *values_in;  /* upsert: pinned host [n][dim] */
+  float *values_out;       /* find: pinned host [n][dim] */
+  uint8_t *flags;          /* pinned host [n] (found / status) or NULL */
+} hkv_serve_request;
+typedef struct {
+  double admit_s;
+  double done_s;
+  uint64_t round;
+} hkv_serve_result;
+hkv_status hkv_serve_create(const hkv_table_t *tables, int n_tables, uint64_t ring_keys,
+                            uint64_t hbm_budget_bytes, int max_inflight, hkv_server_t *out);
+uint64_t hkv_serve_hbm_bytes(hkv_server_t s);
+hkv_status hkv_serve_run(hkv_server_t s, const hkv_serve_request *reqs, uint64_t n_req,
+                         int batched, int use_graph, hkv_serve_result *results,
+                         hkv_stream_t stream);
+hkv_status hkv_serve_destroy(hkv_server_t s);
+
 /* Measurement hook. While enabled, every kernel the library launches for
  * this table is bracketed by two CUDA events recorded on the launching
  * stream. hkv_profile_read waits for those events and returns, per kernel

@@ -45,6 +45,15 @@ class BatchOp(ctypes.Structure):
 
 OP_NONE, OP_FIND, OP_UPSERT = 0, 1, 2
 
+
+class ServeRequest(ctypes.Structure):
+    _fields_ = [("arrival_s", ctypes.c_double), ("table", _i32), ("op", _i32), ("n", _u64),
+                ("keys", _vp), ("values_in", _vp), ("values_out", _vp), ("flags", _vp)]
+
+
+class ServeResult(ctypes.Structure):
+    _fields_ = [("admit_s", ctypes.c_double), ("done_s", ctypes.c_double), ("round", _u64)]
+
 SIGNATURES = {
     "hkv_create": (_i32, [ctypes.POINTER(Options), ctypes.POINTER(_vp)]),
     "hkv_destroy": (_i32, [_vp]),
@@ -70,6 +79,11 @@ SIGNATURES = {
     "hkv_batch_create": (_i32, [_i32, ctypes.POINTER(_vp), _P64, ctypes.POINTER(_vp)]),
     "hkv_batch_run": (_i32, [_vp, ctypes.POINTER(BatchOp), _i32, _vp]),
     "hkv_batch_destroy": (_i32, [_vp]),
+    "hkv_serve_create": (_i32, [ctypes.POINTER(_vp), _i32, _u64, _u64, _i32, ctypes.POINTER(_vp)]),
+    "hkv_serve_hbm_bytes": (_u64, [_vp]),
+    "hkv_serve_run": (_i32, [_vp, ctypes.POINTER(ServeRequest), _u64, _i32, _i32,
+                             ctypes.POINTER(ServeResult), _vp]),
+    "hkv_serve_destroy": (_i32, [_vp]),
     "hkv_profile_enable": (_i32, [_vp, _i32]),
     "hkv_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), _P64]),
     "hkv_last_error": (ctypes.c_char_p, []),
@@ -383,3 +397,60 @@ class Batch:
             sc = o.get("scores")
             arr[i].scores = sc.data_ptr() if sc is not None else None
         _check(load_library().hkv_batch_run(self._h, arr, int(use_graph), _stream(stream)))
+
+
+class Server:
+    """Serving loop with continuous batching (see hkv_serve_run in
+    include/hkv.h). Requests are ServeRequest structs over pinned host
+    buffers; run() replays them in real time and returns per-request
+    (admit_s, done_s, round)."""
+
+    def __init__(self, tables, ring_keys, hbm_budget_bytes=0, max_inflight=3):
+        L = load_library()
+        self.tables = list(tables)
+        n = len(self.tables)
+        arr = (_vp * n)(*[t.handle.value for t in self.tables])
+        h = ctypes.c_void_p()
+        _check(L.hkv_serve_create(arr, n, ring_keys, hbm_budget_bytes, max_inflight,
+                                  ctypes.byref(h)))
+        self._h = h
+        self.hbm_bytes = L.hkv_serve_hbm_bytes(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(load_library().hkv_serve_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, requests, batched=True, use_graph=True, stream=None):
+        n = len(requests)
+        res = (ServeResult * n)()
+        _check(load_library().hkv_serve_run(self._h, requests, n, int(batched), int(use_graph),
+                                            res, _stream(stream)))
+        return res
+
+
+def make_requests(items):
+    """items: dicts with arrival_s, table, op, keys (pinned int64/uint64 CPU
+    tensor), values (pinned float32 CPU tensor: input for upserts, output for
+    finds), flags (pinned uint8 CPU tensor or None)."""
+    arr = (ServeRequest * len(items))()
+    for i, it in enumerate(items):
+        r = arr[i]
+        r.arrival_s = float(it["arrival_s"])
+        r.table = int(it["table"])
+        r.op = int(it["op"])
+        r.n = int(it["keys"].numel())
+        r.keys = it["keys"].data_ptr()
+        if it["op"] == OP_FIND:
+            r.values_out = it["values"].data_ptr()
+        else:
+            r.values_in = it["values"].data_ptr()
+        fl = it.get("flags")
+        r.flags = fl.data_ptr() if fl is not None else None
+    return arr
