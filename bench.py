@@ -58,7 +58,9 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--find-tpk", type=int, default=0)
     p.add_argument("--update-tpk", type=int, default=0)
-    p.add_argument("--workload", choices=("single", "multi", "serve"), default="single")
+    p.add_argument("--workload", choices=("single", "multi", "serve", "tiered"), default="single")
+    p.add_argument("--tiered-shrink", type=int, default=0,
+                   help="divide the tiered table and its HBM budget by 2^k (small runs)")
     p.add_argument("--serve-budget-gib", type=float, default=120.0)
     p.add_argument("--serve-pool", type=int, default=512)
     p.add_argument("--serve-peak-requests", type=int, default=4096)
@@ -676,6 +678,102 @@ def run_multi(args):
     return out
 
 
+# ------------------------------------------------------------ tiered table
+
+TIERED_WORKLOAD = ("tiered: one table of 2^28 slots, dim 128 fp32 (128 GiB of values) with a 48 GiB "
+                   "HBM value budget and the rest in pinned mapped host memory, TS_FREQ scores "
+                   "(timestamp = batch number), pre-filled to lambda 1.0; per step find then "
+                   "insert_or_assign of the same 2^20 Zipf(0.99) keys over 2^34")
+
+
+def run_tiered(args):
+    import torch
+    import paper_2603_17168_gb300 as hkv
+    from paper_2603_17168_gb300 import workloads as w
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(w.seed_for(4, rank))
+    sh = args.tiered_shrink
+    slots, dim = w.TIERED["slots"] >> sh, w.TIERED["dim"]
+    budget = w.TIERED["hbm_value_bytes"] >> sh
+    t0 = time.time()
+    t = hkv.Table(slots, dim, hkv.CUSTOM_TS_FREQ, hbm_value_budget_bytes=budget)
+    create_s = time.time() - t0
+    batch = args.batch
+    t.set_epoch(1)
+    t1 = time.time()
+    lam = fill_table(t, 1.0, gen, dim)
+    fill_s = time.time() - t1
+    z = w.Zipf(w.TIERED["zipf_alpha"], w.TIERED["universe"])
+    nbat = args.warmup + args.steps
+    keys = [w.zipf_keys_torch(gen, z, batch) for _ in range(nbat)]
+    vals = [torch.randn((batch, dim), device=dev, generator=gen) for _ in range(nbat)]
+    out = torch.empty((batch, dim), device=dev)
+    found = torch.empty(batch, dtype=torch.uint8, device=dev)
+    st = torch.empty(batch, dtype=torch.uint8, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(nbat)]
+
+    def step(i):
+        t.set_epoch(2 + i)
+        ev[i][0].record()
+        t.find(keys[i], out, found)
+        ev[i][1].record()
+        t.insert_or_assign(keys[i], vals[i], status_out=st)
+        ev[i][2].record()
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    t.reset_counters()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.warmup, nbat):
+        step(i)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    c = t.read_counters()
+    f_ms = sum(ev[i][0].elapsed_time(ev[i][1]) for i in range(args.warmup, nbat))
+    u_ms = sum(ev[i][1].elapsed_time(ev[i][2]) for i in range(args.warmup, nbat))
+    attempted = c["inserted"] + c["evicted"] + c["rejected"]
+    # host link reference: pinned host -> device copy bandwidth (copy engine)
+    h = torch.empty(1 << 28, dtype=torch.uint8).pin_memory()
+    d = torch.empty(1 << 28, dtype=torch.uint8, device=dev)
+    d.copy_(h, non_blocking=True)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(5):
+        d.copy_(h, non_blocking=True)
+    b.record()
+    b.synchronize()
+    h2d_gbs = 5 * (1 << 28) / (a.elapsed_time(b) * 1e6)
+    hbm_frac = t.hbm_value_slots / t.capacity
+    res = {"metric": METRIC, "value": round(2 * args.steps * batch / (ms * 1e-3) / 1e9, 4),
+           "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+           "config": {"workload": TIERED_WORKLOAD, "slots": slots, "dim": dim,
+                      "hbm_value_budget_gib": round(budget / (1 << 30), 2),
+                      "host_value_gib": round((t.capacity - t.hbm_value_slots) * dim * 4 / (1 << 30), 2),
+                      "value_slots_in_hbm_frac": round(hbm_frac, 4), "batch": batch,
+                      "create_s": round(create_s, 1), "fill_s": round(fill_s, 1),
+                      "lambda_fill": round(lam, 4)},
+           "find_bkvs": round(args.steps * batch / f_ms / 1e6, 4),
+           "upsert_bkvs": round(args.steps * batch / u_ms / 1e6, 4),
+           "find_hit_rate": round(c["find_hit"] / max(1, c["find_hit"] + c["find_miss"]), 4),
+           "eviction_rate": round(c["evicted"] / max(1, attempted), 4),
+           "rejection_rate": round(c["rejected"] / max(1, attempted), 4),
+           "host_value_bytes_per_step_est": int((1 - hbm_frac) * 4 * dim * (c["find_hit"] + c["updated"]
+                                                 + c["inserted"] + c["evicted"]) / args.steps),
+           "h2d_copy_gbs_reference": round(h2d_gbs, 1)}
+    t.close()
+    return res
+
+
 # ----------------------------------------------------------- serving loop
 
 SERVE_WORKLOAD = ("serving: the 8 multi-table tables (LRU, pre-filled to lambda 1.0) behind the "
@@ -784,6 +882,10 @@ def main(argv=None):
         import __graft_entry__ as g
         g.build()
         res = run_multi(args)
+    elif args.workload == "tiered":
+        import __graft_entry__ as g
+        g.build()
+        res = run_tiered(args)
     elif args.workload == "serve":
         import __graft_entry__ as g
         g.build()

@@ -230,7 +230,14 @@ enum {
   HKV_CNT_INS_LINES = 12,  /* digest lines read by the insert phase */
   HKV_CNT_INS_SCORES = 13, /* 1-KiB score lines read by victim searches */
   HKV_CNT_INS_KEYS = 14,   /* keys read by victim searches (tie-break) */
-  HKV_COUNTER_COUNT = 15
+  HKV_CNT_TIMEOUT_FREE = 15,   /* free-slot claims that ran out of attempts */
+  HKV_CNT_TIMEOUT_EVICT = 16,  /* victim searches that ran out of attempts */
+  HKV_CNT_TIMEOUT_WHY = 17,    /* last such search's last failure: 1 a locked
+                                  candidate, 2 no candidate, 3 lost the CAS,
+                                  4 score changed under the lock, 5 lost a
+                                  free-slot CAS */
+  HKV_CNT_TIMEOUT_KEY = 18,    /* its key */
+  HKV_COUNTER_COUNT = 19
 };
 hkv_status hkv_read_counters(hkv_table_t t, uint64_t *out, hkv_stream_t stream);
 hkv_status hkv_reset_counters(hkv_table_t t, hkv_stream_t stream);

@@ -20,7 +20,8 @@ LRU, LFU, EPOCH_LRU, EPOCH_LFU, CUSTOM, CUSTOM_TS_FREQ = range(6)
 ST_UPDATED, ST_INSERTED, ST_REJECTED = 1, 2, 3
 COUNTER_NAMES = ("find_hit", "find_miss", "unique", "updated", "inserted", "evicted",
                  "rejected", "retries", "find_lines", "find_keys", "upd_lines", "upd_keys",
-                 "ins_lines", "ins_score_lines", "ins_keys")
+                 "ins_lines", "ins_score_lines", "ins_keys", "timeout_free", "timeout_evict",
+                 "timeout_why", "timeout_key")
 KERNEL_NAMES = ("find", "dedup", "update", "insert", "reconcile", "status", "erase", "export",
                 "size")
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "RESERVED_KEY", 3: "DUPLICATE_KEY", 4: "OOM",

@@ -360,7 +360,7 @@ hkv_status hkv_erase(hkv_table_t t, uint64_t n, const uint64_t* keys, hkv_stream
 hkv_status hkv_size(hkv_table_t t, uint64_t* out, hkv_stream_t stream) {
   if (bad(t) || !out) return fail(HKV_ERR_INVALID_ARG, "size arguments");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  unsigned long long* d = t->dev.counters + 24;  // spare words after the counters
+  unsigned long long* d = t->dev.counters + 28;  // spare words after the counters
   {
     auto lk = t->sched.acquire(kReader, s);
     hkv_status rc = launch_size(t, d, s);

@@ -278,10 +278,17 @@ __device__ __forceinline__ int held_slot(int lane, int q) {
 }
 
 // Write (key, value, score, digest) into a slot this warp holds LOCKED, then
-// publish the key. Values are written by all lanes; lane 0 owns the rest.
+// publish the key. The digest and score go first, so other claimers see the
+// slot taken at once even while a value row is still travelling to host
+// memory; every lane fences its value stores before lane 0 publishes the
+// key, so no later writer of the slot can be overtaken by them.
 template <bool VEC16>
 __device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_t key, uint64_t sc,
                                           uint32_t dg, const float* src, int lane) {
+  if (lane == 0) {
+    t.digests[g] = (uint8_t)dg;
+    __stcg(reinterpret_cast<unsigned long long*>(t.scores + g), (unsigned long long)sc);
+  }
   float* dst = value_ptr(t, g);
   if (VEC16) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
@@ -290,12 +297,10 @@ __device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_
   } else {
     for (uint32_t j = lane; j < t.dim; j += 32) __stcg(dst + j, __ldg(src + j));
   }
-  if (lane == 0) {
-    __stcg(reinterpret_cast<unsigned long long*>(t.scores + g), (unsigned long long)sc);
-    t.digests[g] = (uint8_t)dg;
-    __threadfence();
+  __threadfence();
+  __syncwarp();
+  if (lane == 0)
     atomicExch(reinterpret_cast<unsigned long long*>(t.keys + g), (unsigned long long)key);
-  }
   __syncwarp();
 }
 
@@ -328,11 +333,13 @@ __device__ __forceinline__ void scan_free(const uint8_t* line, unsigned start, i
   }
 }
 
-// One thread writes (value, score, digest) into a slot it holds LOCKED and
-// publishes the key.
+// One thread writes (digest, score, value) into a slot it holds LOCKED and
+// publishes the key after a fence (digest first: see fill_slot).
 template <bool VEC16>
 __device__ __forceinline__ void fill_slot_thread(const TableDev& t, uint64_t g, uint64_t key,
                                                  uint64_t sc, uint32_t dg, const float* src) {
+  t.digests[g] = (uint8_t)dg;
+  __stcg(reinterpret_cast<unsigned long long*>(t.scores + g), (unsigned long long)sc);
   float* dst = value_ptr(t, g);
   if (VEC16) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
@@ -341,10 +348,16 @@ __device__ __forceinline__ void fill_slot_thread(const TableDev& t, uint64_t g, 
   } else {
     for (uint32_t j = 0; j < t.dim; ++j) __stcg(dst + j, __ldg(src + j));
   }
-  __stcg(reinterpret_cast<unsigned long long*>(t.scores + g), (unsigned long long)sc);
-  t.digests[g] = (uint8_t)dg;
   __threadfence();
   atomicExch(reinterpret_cast<unsigned long long*>(t.keys + g), (unsigned long long)key);
+}
+
+// Back-off before retry `attempt` (> 0): exponential up to ~16 us, with
+// per-key jitter so colliding warps fall apart. With kMaxClaimAttempts
+// retries a claim waits at most ~65 ms before it gives up.
+__device__ __forceinline__ void claim_backoff(int attempt, uint64_t h) {
+  const unsigned base = 32u << (attempt < 9 ? attempt : 9);
+  __nanosleep(base + ((unsigned)(h >> 17) & 255u));
 }
 
 constexpr int kPrefetchAhead = 3;  // victim searches whose lines are prefetched ahead
@@ -393,7 +406,7 @@ __global__ void __launch_bounds__(kInsThreads, 4)
     bool pending = miss, full = false;
     for (int attempt = 0; __any_sync(kFull, pending) && attempt < kMaxClaimAttempts; ++attempt) {
       if (!pending) continue;
-      if (attempt) __nanosleep((32u << (attempt < 6 ? attempt : 6)) + ((unsigned)(my_h >> 17) & 255u));
+      if (attempt) claim_backoff(attempt, my_h);
       const unsigned start = (unsigned)(my_h >> 40) + (unsigned)attempt;
       int f1, c1, f2 = 0, c2 = -1;
       scan_free(t.digests + my_b1 * kSlots, start, f1, c1);
@@ -422,6 +435,9 @@ __global__ void __launch_bounds__(kInsThreads, 4)
     }
     if (pending) {  // bounded wait ran out
       latch_error(t.err, HKV_ERR_TIMEOUT);
+      atomicAdd(t.counters + HKV_CNT_TIMEOUT_FREE, 1ull);
+      atomicExch(t.counters + HKV_CNT_TIMEOUT_WHY, 5ull);
+      atomicExch(t.counters + HKV_CNT_TIMEOUT_KEY, (unsigned long long)my_key);
       s.evk[my_u] = kEmptyKey;
       s.tstatus[my_e] = HKV_ST_REJECTED;
     }
@@ -477,9 +493,10 @@ __global__ void __launch_bounds__(kInsThreads, 4)
       const uint32_t dg = digest_from_hash(h);
       uint8_t outcome = HKV_ST_REJECTED;
       uint64_t victim_key = kEmptyKey;
+      unsigned why = 0;
       int attempt = 0;
       for (; attempt < kMaxClaimAttempts; ++attempt) {
-        if (attempt) __nanosleep((32u << (attempt < 6 ? attempt : 6)) + ((unsigned)(h >> 17) & 255u));
+        if (attempt) claim_backoff(attempt, h);
         // Buckets stay full during a batch (no erase runs beside an
         // inserter), so the victim search needs no free-slot re-check.
         score_lines += two ? 2 : 1;
@@ -525,7 +542,11 @@ __global__ void __launch_bounds__(kInsThreads, 4)
           }
         }
         const unsigned long long kmin = shfl_min_u64(kbest);
-        if (__any_sync(kFull, busy) || kmin == ~0ull) { retries += lane == 0; continue; }
+        if (__any_sync(kFull, busy) || kmin == ~0ull) {
+          why = kmin == ~0ull ? 2u : 1u;
+          retries += lane == 0;
+          continue;
+        }
         // Admission control: admit iff (s, k) > (s_min, k_min).
         if (!sk_less(smin, kmin, sc, key)) {
           outcome = HKV_ST_REJECTED;
@@ -534,7 +555,7 @@ __global__ void __launch_bounds__(kInsThreads, 4)
         }
         const unsigned own = __ballot_sync(kFull, qbest >= 0 && kbest == kmin);
         const int owner = __ffs(own) - 1;
-        int ok = 0;
+        int ok = 0, stale = 0;
         uint64_t g = 0;
         if (lane == owner) {
           const uint64_t bq = qbest < 4 ? b1 : b2;
@@ -545,11 +566,16 @@ __global__ void __launch_bounds__(kInsThreads, 4)
           if (ok && __ldcg(reinterpret_cast<const unsigned long long*>(t.scores + g)) != smin) {
             atomicExch(reinterpret_cast<unsigned long long*>(t.keys + g), kmin);
             ok = 0;
+            stale = 1;
           }
         }
         ok = __shfl_sync(kFull, ok, owner);
         g = __shfl_sync(kFull, g, owner);
-        if (!ok) { retries += lane == 0; continue; }
+        if (!ok) {
+          why = __shfl_sync(kFull, stale, owner) ? 4u : 3u;
+          retries += lane == 0;
+          continue;
+        }
         if (lane == 0) s.evs[u] = smin;
         if (s.evv) {
           const float* vsrc = value_ptr(t, g);
@@ -562,7 +588,12 @@ __global__ void __launch_bounds__(kInsThreads, 4)
         break;
       }
       if (lane == 0) {
-        if (attempt == kMaxClaimAttempts) latch_error(t.err, HKV_ERR_TIMEOUT);
+        if (attempt == kMaxClaimAttempts) {
+          latch_error(t.err, HKV_ERR_TIMEOUT);
+          atomicAdd(t.counters + HKV_CNT_TIMEOUT_EVICT, 1ull);
+          atomicExch(t.counters + HKV_CNT_TIMEOUT_WHY, (unsigned long long)why);
+          atomicExch(t.counters + HKV_CNT_TIMEOUT_KEY, (unsigned long long)key);
+        }
         s.evk[u] = victim_key;
         s.tstatus[e] = outcome;
       }
