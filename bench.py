@@ -365,6 +365,7 @@ def run_ours(args):
     for li, t in enumerate(tables):
         prof = t.profile_read()
         c = per_lambda[li]["_counters"]
+        per_lambda[li]["kernel_ms"] = {k: round(v[0], 4) for k, v in prof.items()}
         for kind, (kms, launches) in prof.items():
             e = kinds.setdefault(kind, {"ms": 0.0, "launches": 0, "bytes": 0.0})
             e["ms"] += kms

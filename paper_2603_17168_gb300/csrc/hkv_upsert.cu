@@ -277,11 +277,19 @@ __device__ __forceinline__ int held_slot(int lane, int q) {
   return (q >> 1) * 64 + 2 * lane + (q & 1);
 }
 
+// Publish a slot's key with a release store at GPU scope: every write the
+// publishing thread has made, or has observed through a warp barrier (the
+// other lanes' value stores), becomes visible before the key does.
+__device__ __forceinline__ void publish_key(uint64_t* addr, uint64_t key) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(addr), "l"(key) : "memory");
+}
+
 // Write (key, value, score, digest) into a slot this warp holds LOCKED, then
 // publish the key. The digest and score go first, so other claimers see the
 // slot taken at once even while a value row is still travelling to host
-// memory; every lane fences its value stores before lane 0 publishes the
-// key, so no later writer of the slot can be overtaken by them.
+// memory; the lanes' value stores are ordered before the key by the warp
+// barrier and the release, so no later writer of the slot can be overtaken
+// by them.
 template <bool VEC16>
 __device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_t key, uint64_t sc,
                                           uint32_t dg, const float* src, int lane) {
@@ -297,10 +305,8 @@ __device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_
   } else {
     for (uint32_t j = lane; j < t.dim; j += 32) __stcg(dst + j, __ldg(src + j));
   }
-  __threadfence();
   __syncwarp();
-  if (lane == 0)
-    atomicExch(reinterpret_cast<unsigned long long*>(t.keys + g), (unsigned long long)key);
+  if (lane == 0) publish_key(t.keys + g, key);
   __syncwarp();
 }
 
@@ -334,7 +340,7 @@ __device__ __forceinline__ void scan_free(const uint8_t* line, unsigned start, i
 }
 
 // One thread writes (digest, score, value) into a slot it holds LOCKED and
-// publishes the key after a fence (digest first: see fill_slot).
+// publishes the key with a release store (digest first: see fill_slot).
 template <bool VEC16>
 __device__ __forceinline__ void fill_slot_thread(const TableDev& t, uint64_t g, uint64_t key,
                                                  uint64_t sc, uint32_t dg, const float* src) {
@@ -348,8 +354,7 @@ __device__ __forceinline__ void fill_slot_thread(const TableDev& t, uint64_t g, 
   } else {
     for (uint32_t j = 0; j < t.dim; ++j) __stcg(dst + j, __ldg(src + j));
   }
-  __threadfence();
-  atomicExch(reinterpret_cast<unsigned long long*>(t.keys + g), (unsigned long long)key);
+  publish_key(t.keys + g, key);
 }
 
 // Back-off before retry `attempt` (> 0): exponential up to ~16 us, with
@@ -458,6 +463,7 @@ __global__ void __launch_bounds__(kInsThreads, 4)
             bulk_prefetch_l2(t.scores + my_b2 * kSlots, kSlots * 8);
             bulk_prefetch_l2(t.keys + my_b2 * kSlots, kSlots * 8);
           }
+          if (VEC16) bulk_prefetch_l2(values + (uint64_t)my_i * t.dim, t.dim * 4);
         }
       }
     }
@@ -477,6 +483,7 @@ __global__ void __launch_bounds__(kInsThreads, 4)
               bulk_prefetch_l2(t.scores + my_b2 * kSlots, kSlots * 8);
               bulk_prefetch_l2(t.keys + my_b2 * kSlots, kSlots * 8);
             }
+            if (VEC16) bulk_prefetch_l2(values + (uint64_t)my_i * t.dim, t.dim * 4);
           }
         }
       }
@@ -499,54 +506,55 @@ __global__ void __launch_bounds__(kInsThreads, 4)
         if (attempt) claim_backoff(attempt, h);
         // Buckets stay full during a batch (no erase runs beside an
         // inserter), so the victim search needs no free-slot re-check.
+        // Each lane reads its slots' scores and keys as coalesced pairs
+        // (slots 2l, 2l+1 and 64+2l, 65+2l of each candidate bucket) and keeps
+        // its smallest (score, key); one warp argmin gives the victim. A slot
+        // locked by another warp is mid-replacement: if its visible score
+        // does not exceed the minimum, its next (score, key) could be the
+        // minimum, so re-read later rather than choose around it.
         score_lines += two ? 2 : 1;
-        unsigned long long sv[8];
-        {
-          const ulonglong2* p1 = reinterpret_cast<const ulonglong2*>(t.scores + b1 * kSlots);
-          const ulonglong2 a = __ldcg(p1 + lane), d = __ldcg(p1 + 32 + lane);
-          sv[0] = a.x; sv[1] = a.y; sv[2] = d.x; sv[3] = d.y;
-          if (two) {
-            const ulonglong2* p2 = reinterpret_cast<const ulonglong2*>(t.scores + b2 * kSlots);
-            const ulonglong2 f = __ldcg(p2 + lane), q = __ldcg(p2 + 32 + lane);
-            sv[4] = f.x; sv[5] = f.y; sv[6] = q.x; sv[7] = q.y;
-          } else {
-            sv[4] = sv[5] = sv[6] = sv[7] = ~0ull;
+        unsigned long long bs = ~0ull, bk = ~0ull, lockmin = ~0ull;
+        int bq = -1;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          if (half == 1 && !two) break;
+          const uint64_t bb = half ? b2 : b1;
+          const ulonglong2* ps = reinterpret_cast<const ulonglong2*>(t.scores + bb * kSlots);
+          const ulonglong2* pk = reinterpret_cast<const ulonglong2*>(t.keys + bb * kSlots);
+          const ulonglong2 s0 = __ldcg(ps + lane), s1 = __ldcg(ps + 32 + lane);
+          const ulonglong2 k0 = __ldcg(pk + lane), k1 = __ldcg(pk + 32 + lane);
+          const unsigned long long sq[4] = {s0.x, s0.y, s1.x, s1.y};
+          const unsigned long long kq[4] = {k0.x, k0.y, k1.x, k1.y};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (kq[j] >= kLockedKey) {
+              lockmin = sq[j] < lockmin ? sq[j] : lockmin;
+            } else if (sk_less(sq[j], kq[j], bs, bk)) {
+              bs = sq[j];
+              bk = kq[j];
+              bq = half * 4 + j;
+            }
           }
         }
-        unsigned long long lmin = sv[0];
+        kreads += two ? 8 : 4;
+        unsigned long long smin = bs, kmin = bk;
 #pragma unroll
-        for (int q = 1; q < 8; ++q) lmin = sv[q] < lmin ? sv[q] : lmin;
-        const unsigned long long smin = shfl_min_u64(lmin);
-        // Tie-break by key among the slots holding the minimum score, reading
-        // key pairs next to each other. A slot locked by another warp is
-        // mid-replacement and its next value is not known yet: re-read later
-        // rather than choose around it.
-        unsigned long long kbest = ~0ull;
-        int qbest = -1;
-        bool busy = false;
-#pragma unroll
-        for (int pr = 0; pr < 4; ++pr) {
-          if (pr >= 2 && !two) break;
-          if (sv[2 * pr] != smin && sv[2 * pr + 1] != smin) continue;
-          const uint64_t bq = pr < 2 ? b1 : b2;
-          const ulonglong2 kp = __ldcg(reinterpret_cast<const ulonglong2*>(t.keys + bq * kSlots) +
-                                       (pr & 1) * 32 + lane);
-          kreads += 2;
-#pragma unroll
-          for (int h2 = 0; h2 < 2; ++h2) {
-            const int q = 2 * pr + h2;
-            const unsigned long long kq = h2 ? kp.y : kp.x;
-            if (sv[q] != smin) continue;
-            if (kq >= kLockedKey) { busy = true; continue; }
-            if (kq < kbest) { kbest = kq; qbest = q; }
+        for (int o = 16; o; o >>= 1) {
+          const unsigned long long os = __shfl_xor_sync(kFull, smin, o);
+          const unsigned long long ok2 = __shfl_xor_sync(kFull, kmin, o);
+          if (sk_less(os, ok2, smin, kmin)) {
+            smin = os;
+            kmin = ok2;
           }
         }
-        const unsigned long long kmin = shfl_min_u64(kbest);
-        if (__any_sync(kFull, busy) || kmin == ~0ull) {
+        lockmin = shfl_min_u64(lockmin);
+        if (lockmin <= smin || kmin == ~0ull) {
           why = kmin == ~0ull ? 2u : 1u;
           retries += lane == 0;
           continue;
         }
+        const unsigned long long kbest = bk;
+        const int qbest = bq;
         // Admission control: admit iff (s, k) > (s_min, k_min).
         if (!sk_less(smin, kmin, sc, key)) {
           outcome = HKV_ST_REJECTED;
@@ -558,8 +566,8 @@ __global__ void __launch_bounds__(kInsThreads, 4)
         int ok = 0, stale = 0;
         uint64_t g = 0;
         if (lane == owner) {
-          const uint64_t bq = qbest < 4 ? b1 : b2;
-          g = bq * kSlots + (uint64_t)held_slot(lane, qbest & 3);
+          const uint64_t bqk = qbest < 4 ? b1 : b2;
+          g = bqk * kSlots + (uint64_t)held_slot(lane, qbest & 3);
           ok = atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + g), kmin, kLockedKey) == kmin;
           // A score and key read from two different occupants of the slot
           // would show here as a changed score: release and start over.
