@@ -217,15 +217,18 @@ def kernel_bytes(kind: str, c: dict, n_calls: int, batch: int, dim: int) -> floa
         return (n_calls * batch * 9 + 128 * c["find_lines"] + S * c["find_keys"]
                 + 2 * D * c["find_hit"])
     u = c["unique"]
+    uc = c.get("upd_claims", 0)
     if kind == "update":
-        miss = u - c["updated"]
+        # probe + in-place update of residents, and the free-slot claims made here
+        miss = u - c["updated"] - uc
         return (u * (4 + S) + 128 * c["upd_lines"] + S * c["upd_keys"]
-                + c["updated"] * (2 * D + 2 * S + S) + miss * 4)
+                + c["updated"] * (2 * D + 2 * S + S) + miss * 4 * 4
+                + 128 * c.get("upd_claim_lines", 0) + uc * (3 * S + 2 * D + S))
     if kind == "insert":
-        nm = c["inserted"] + c["evicted"] + c["rejected"]
-        claimed = c["inserted"] + c["evicted"]
-        return (nm * (4 + S + S) + 128 * c["ins_lines"] + 1024 * c["ins_score_lines"]
-                + S * c["ins_keys"] + claimed * (3 * S + 2 * D) + c["evicted"] * S)
+        ins = c["inserted"] - uc
+        nm = ins + c["evicted"] + c["rejected"]
+        return (nm * (4 * 4 + S + S) + 128 * c["ins_lines"] + 1024 * c["ins_score_lines"]
+                + S * c["ins_keys"] + (ins + c["evicted"]) * (3 * S + 2 * D) + c["evicted"] * S)
     if kind == "dedup":
         return n_calls * batch * (8 + 4) + u * 2 * S
     if kind == "status":

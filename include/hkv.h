@@ -219,7 +219,7 @@ enum {
   HKV_CNT_FIND_MISS = 1,
   HKV_CNT_UNIQUE = 2,      /* distinct keys of upsert / assign batches */
   HKV_CNT_UPDATED = 3,
-  HKV_CNT_INSERTED = 4,    /* claimed a free slot */
+  HKV_CNT_INSERTED = 4,    /* claimed a free slot (either phase) */
   HKV_CNT_EVICTED = 5,     /* replaced a minimum entry */
   HKV_CNT_REJECTED = 6,    /* refused by admission */
   HKV_CNT_RETRIES = 7,     /* slot-claim retries after a lost race */
@@ -237,7 +237,10 @@ enum {
                                   4 score changed under the lock, 5 lost a
                                   free-slot CAS */
   HKV_CNT_TIMEOUT_KEY = 18,    /* its key */
-  HKV_COUNTER_COUNT = 19
+  HKV_CNT_UPD_CLAIMS = 19,     /* free-slot claims made by the update phase
+                                  (included in HKV_CNT_INSERTED) */
+  HKV_CNT_UPD_CLAIM_LINES = 20, /* digest lines those claims read */
+  HKV_COUNTER_COUNT = 21
 };
 hkv_status hkv_read_counters(hkv_table_t t, uint64_t *out, hkv_stream_t stream);
 hkv_status hkv_reset_counters(hkv_table_t t, hkv_stream_t stream);

@@ -21,7 +21,7 @@ ST_UPDATED, ST_INSERTED, ST_REJECTED = 1, 2, 3
 COUNTER_NAMES = ("find_hit", "find_miss", "unique", "updated", "inserted", "evicted",
                  "rejected", "retries", "find_lines", "find_keys", "upd_lines", "upd_keys",
                  "ins_lines", "ins_score_lines", "ins_keys", "timeout_free", "timeout_evict",
-                 "timeout_why", "timeout_key")
+                 "timeout_why", "timeout_key", "upd_claims", "upd_claim_lines")
 KERNEL_NAMES = ("find", "dedup", "update", "insert", "reconcile", "status", "erase", "export",
                 "size")
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "RESERVED_KEY", 3: "DUPLICATE_KEY", 4: "OOM",

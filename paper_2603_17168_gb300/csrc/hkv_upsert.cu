@@ -179,135 +179,11 @@ __global__ void __launch_bounds__(kDedupThreads)
   flush_counts(t, which, vals);
 }
 
-// ----------------------------------------------------------- phase U probe
-
-constexpr int kUpdThreads = 256;
-
-template <int G, bool VEC16, bool UPSERT>
-__global__ void __launch_bounds__(kUpdThreads)
-    update_kernel(TableDev t, Scratch s, const float* __restrict__ values,
-                  const uint64_t* __restrict__ scores_in, ScoreCtx ctx) {
-  if (aborted(s)) return;
-  if (s.d) {
-    values = s.d->values_in;
-    scores_in = s.d->scores;
-    ctx.step = s.d->step;
-    ctx.epoch = s.d->epoch;
-  }
-  constexpr int KPW = 32 / G;
-  const int lane = threadIdx.x & 31;
-  const int lane_g = lane & (G - 1);
-  const int group_base = lane & ~(G - 1);
-  const unsigned group_bits = G == 32 ? kFull : (((1u << G) - 1u) << group_base);
-  const uint64_t warp = (blockIdx.x * (uint64_t)kUpdThreads + threadIdx.x) >> 5;
-  const uint64_t nwarps = ((uint64_t)gridDim.x * kUpdThreads) >> 5;
-  const uint64_t nu = s.cnt[kCntUnique];
-  unsigned updated = 0, lines = 0, kreads = 0;
-
-  for (uint64_t base = warp * KPW; base < nu; base += nwarps * KPW) {
-    const uint64_t u = base + (lane / G);
-    const bool active = u < nu;
-    const uint32_t e = active ? s.ulist[u] : 0;
-    const uint64_t key = active ? s.tab[e].key : kEmptyKey;
-    const uint64_t h = fmix64(key);
-    uint64_t b = h & t.bucket_mask;
-    const uint32_t pat4 = digest_from_hash(h) * 0x01010101u;
-    int slot = probe_bucket<G, false>(t, b, key, pat4, active, lane_g, group_bits, group_base,
-                                      kreads);
-    lines += active && lane_g == 0;
-    if (t.dual) {
-      const uint64_t b2 = second_bucket(t, key);
-      const bool need = active && slot < 0 && b2 != b;
-      lines += need && lane_g == 0;
-      if (__any_sync(kFull, need)) {
-        const int s2 = probe_bucket<G, false>(t, b2, key, pat4, need, lane_g, group_bits,
-                                              group_base, kreads);
-        if (need && s2 >= 0) {
-          slot = s2;
-          b = b2;
-        }
-      }
-    }
-    const bool hit = active && slot >= 0;
-    if (active) {
-      const uint64_t i = ~s.tab[e].nlast;
-      const uint64_t m = (uint64_t)s.tab[e].cnt_m1 + 1;
-      if (hit) {
-        const uint64_t g = b * kSlots + (uint64_t)slot;
-        if (values) copy_row<G, VEC16, false>(value_ptr(t, g), values + i * t.dim, t.dim, lane_g);
-        if (lane_g == 0) {
-          const uint64_t old = t.scores[g];
-          t.scores[g] = policy_score(t.policy, true, old, m, scores_in != nullptr,
-                                     scores_in ? __ldg(scores_in + i) : 0, ctx);
-          s.tstatus[e] = HKV_ST_UPDATED;
-          updated++;
-        }
-      }
-      if (UPSERT && lane_g == 0) {
-        s.mflag[u] = hit ? 0 : 1;
-        if (!hit) {
-          s.mkey[u] = key;
-          s.mi[u] = (uint32_t)i;
-          s.mm[u] = (uint32_t)m;
-        }
-      }
-    }
-  }
-  const int which[3] = {HKV_CNT_UPDATED, HKV_CNT_UPD_LINES, HKV_CNT_UPD_KEYS};
-  const unsigned vals[3] = {updated, lines, kreads};
-  flush_counts(t, which, vals);
-}
-
-// --------------------------------------------------------- phase I insert
-
-constexpr int kInsThreads = 256;
-
-__device__ __forceinline__ unsigned long long shfl_min_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    const unsigned long long w = __shfl_xor_sync(kFull, v, o);
-    v = w < v ? w : v;
-  }
-  return v;
-}
-
-// Slot of a bucket held by `lane` in the coalesced score layout: q = 0, 1
-// are slots 2*lane, 2*lane + 1; q = 2, 3 are 64 + 2*lane, 65 + 2*lane.
-__device__ __forceinline__ int held_slot(int lane, int q) {
-  return (q >> 1) * 64 + 2 * lane + (q & 1);
-}
-
 // Publish a slot's key with a release store at GPU scope: every write the
 // publishing thread has made, or has observed through a warp barrier (the
 // other lanes' value stores), becomes visible before the key does.
 __device__ __forceinline__ void publish_key(uint64_t* addr, uint64_t key) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(addr), "l"(key) : "memory");
-}
-
-// Write (key, value, score, digest) into a slot this warp holds LOCKED, then
-// publish the key. The digest and score go first, so other claimers see the
-// slot taken at once even while a value row is still travelling to host
-// memory; the lanes' value stores are ordered before the key by the warp
-// barrier and the release, so no later writer of the slot can be overtaken
-// by them.
-template <bool VEC16>
-__device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_t key, uint64_t sc,
-                                          uint32_t dg, const float* src, int lane) {
-  if (lane == 0) {
-    t.digests[g] = (uint8_t)dg;
-    __stcg(reinterpret_cast<unsigned long long*>(t.scores + g), (unsigned long long)sc);
-  }
-  float* dst = value_ptr(t, g);
-  if (VEC16) {
-    const float4* s4 = reinterpret_cast<const float4*>(src);
-    float4* d4 = reinterpret_cast<float4*>(dst);
-    for (uint32_t j = lane; j < (t.dim >> 2); j += 32) __stcg(d4 + j, __ldg(s4 + j));
-  } else {
-    for (uint32_t j = lane; j < t.dim; j += 32) __stcg(dst + j, __ldg(src + j));
-  }
-  __syncwarp();
-  if (lane == 0) publish_key(t.keys + g, key);
-  __syncwarp();
 }
 
 // L2 prefetch of a contiguous range with one TMA bulk instruction
@@ -365,6 +241,189 @@ __device__ __forceinline__ void claim_backoff(int attempt, uint64_t h) {
   __nanosleep(base + ((unsigned)(h >> 17) & 255u));
 }
 
+// Phase I's free-slot claim for one key, run by one thread (Algorithm 2
+// lines 6-9; Algorithm 3 phase D1: a free slot of the less occupied
+// candidate, b1 on equal occupancy). Returns 0 when the key was placed (or
+// the bounded wait ran out and the error was latched), 2 when every
+// candidate bucket is full and the key needs a victim search.
+template <bool VEC16>
+__device__ __forceinline__ uint8_t claim_free_slot(const TableDev& t, const Scratch& s, uint32_t e,
+                                                   uint64_t key, uint64_t h, uint64_t sc,
+                                                   const float* src, unsigned& lines,
+                                                   unsigned& inserted, unsigned& retries) {
+  const uint64_t b1 = h & t.bucket_mask;
+  const uint64_t b2 = t.dual ? second_bucket(t, key) : b1;
+  const bool two = b2 != b1;
+  for (int attempt = 0; attempt < kMaxClaimAttempts; ++attempt) {
+    if (attempt) claim_backoff(attempt, h);
+    const unsigned start = (unsigned)(h >> 40) + (unsigned)attempt;
+    int f1, c1, f2 = 0, c2 = -1;
+    scan_free(t.digests + b1 * kSlots, start, f1, c1);
+    lines++;
+    if (two) {
+      scan_free(t.digests + b2 * kSlots, start, f2, c2);
+      lines++;
+    }
+    if (f1 == 0 && f2 == 0) return 2;
+    const bool use1 = !two || f1 >= f2;
+    const uint64_t g = (use1 ? b1 : b2) * kSlots + (uint64_t)(use1 ? c1 : c2);
+    if (atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + g), kEmptyKey, kLockedKey) !=
+        kEmptyKey) {
+      retries++;
+      continue;
+    }
+    fill_slot_thread<VEC16>(t, g, key, sc, digest_from_hash(h), src);
+    s.tstatus[e] = HKV_ST_INSERTED;
+    inserted++;
+    return 0;
+  }
+  latch_error(t.err, HKV_ERR_TIMEOUT);
+  atomicAdd(t.counters + HKV_CNT_TIMEOUT_FREE, 1ull);
+  atomicExch(t.counters + HKV_CNT_TIMEOUT_WHY, 5ull);
+  atomicExch(t.counters + HKV_CNT_TIMEOUT_KEY, (unsigned long long)key);
+  s.tstatus[e] = HKV_ST_REJECTED;
+  return 0;
+}
+
+// ----------------------------------------------------------- phase U probe
+
+constexpr int kUpdThreads = 256;
+
+template <int G, bool VEC16, bool UPSERT>
+__global__ void __launch_bounds__(kUpdThreads, 4)
+    update_kernel(TableDev t, Scratch s, const float* __restrict__ values,
+                  const uint64_t* __restrict__ scores_in, ScoreCtx ctx) {
+  if (aborted(s)) return;
+  if (s.d) {
+    values = s.d->values_in;
+    scores_in = s.d->scores;
+    ctx.step = s.d->step;
+    ctx.epoch = s.d->epoch;
+  }
+  constexpr int KPW = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int lane_g = lane & (G - 1);
+  const int group_base = lane & ~(G - 1);
+  const unsigned group_bits = G == 32 ? kFull : (((1u << G) - 1u) << group_base);
+  const uint64_t warp = (blockIdx.x * (uint64_t)kUpdThreads + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * kUpdThreads) >> 5;
+  const uint64_t nu = s.cnt[kCntUnique];
+  unsigned updated = 0, lines = 0, kreads = 0, inserted = 0, ins_lines = 0, retries = 0;
+
+  for (uint64_t base = warp * KPW; base < nu; base += nwarps * KPW) {
+    const uint64_t u = base + (lane / G);
+    const bool active = u < nu;
+    const uint32_t e = active ? s.ulist[u] : 0;
+    const uint64_t key = active ? s.tab[e].key : kEmptyKey;
+    const uint64_t h = fmix64(key);
+    uint64_t b = h & t.bucket_mask;
+    const uint32_t pat4 = digest_from_hash(h) * 0x01010101u;
+    int slot = probe_bucket<G, false>(t, b, key, pat4, active, lane_g, group_bits, group_base,
+                                      kreads);
+    lines += active && lane_g == 0;
+    if (t.dual) {
+      const uint64_t b2 = second_bucket(t, key);
+      const bool need = active && slot < 0 && b2 != b;
+      lines += need && lane_g == 0;
+      if (__any_sync(kFull, need)) {
+        const int s2 = probe_bucket<G, false>(t, b2, key, pat4, need, lane_g, group_bits,
+                                              group_base, kreads);
+        if (need && s2 >= 0) {
+          slot = s2;
+          b = b2;
+        }
+      }
+    }
+    const bool hit = active && slot >= 0;
+    if (active) {
+      const uint64_t i = ~s.tab[e].nlast;
+      const uint64_t m = (uint64_t)s.tab[e].cnt_m1 + 1;
+      if (hit) {
+        const uint64_t g = b * kSlots + (uint64_t)slot;
+        if (values) copy_row<G, VEC16, false>(value_ptr(t, g), values + i * t.dim, t.dim, lane_g);
+        if (lane_g == 0) {
+          const uint64_t old = t.scores[g];
+          t.scores[g] = policy_score(t.policy, true, old, m, scores_in != nullptr,
+                                     scores_in ? __ldg(scores_in + i) : 0, ctx);
+          s.tstatus[e] = HKV_ST_UPDATED;
+          updated++;
+        }
+      }
+      if (UPSERT && lane_g == 0) {
+        // mflag: 0 placed (updated, or claimed here), 1 miss left to the
+        // insert kernel, 2 miss whose candidate buckets are all full
+        uint8_t flag = hit ? 0 : 1;
+        if constexpr (G == 1) {
+          // A miss claims its free slot right here: a claim into an empty
+          // slot cannot race the in-place updates of this phase (they
+          // touch other slots), only evictions must wait for phase U.
+          if (!hit) {
+            const uint64_t sc = policy_score(t.policy, false, 0, m, scores_in != nullptr,
+                                             scores_in ? __ldg(scores_in + i) : 0, ctx);
+            flag = claim_free_slot<VEC16>(t, s, e, key, h, sc, values + i * t.dim, ins_lines,
+                                          inserted, retries);
+          }
+        }
+        s.mflag[u] = flag;
+        if (flag) {
+          s.mkey[u] = key;
+          s.mi[u] = (uint32_t)i;
+          s.mm[u] = (uint32_t)m;
+        }
+      }
+    }
+  }
+  const int which[7] = {HKV_CNT_UPDATED, HKV_CNT_UPD_LINES, HKV_CNT_UPD_KEYS, HKV_CNT_INSERTED,
+                        HKV_CNT_UPD_CLAIMS, HKV_CNT_UPD_CLAIM_LINES, HKV_CNT_RETRIES};
+  const unsigned vals[7] = {updated, lines, kreads, inserted, inserted, ins_lines, retries};
+  flush_counts(t, which, vals);
+}
+
+// --------------------------------------------------------- phase I insert
+
+constexpr int kInsThreads = 256;
+
+__device__ __forceinline__ unsigned long long shfl_min_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(kFull, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+
+// Slot of a bucket held by `lane` in the coalesced score layout: q = 0, 1
+// are slots 2*lane, 2*lane + 1; q = 2, 3 are 64 + 2*lane, 65 + 2*lane.
+__device__ __forceinline__ int held_slot(int lane, int q) {
+  return (q >> 1) * 64 + 2 * lane + (q & 1);
+}
+
+// Write (key, value, score, digest) into a slot this warp holds LOCKED, then
+// publish the key. The digest and score go first, so other claimers see the
+// slot taken at once even while a value row is still travelling to host
+// memory; the lanes' value stores are ordered before the key by the warp
+// barrier and the release, so no later writer of the slot can be overtaken
+// by them.
+template <bool VEC16>
+__device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_t key, uint64_t sc,
+                                          uint32_t dg, const float* src, int lane) {
+  if (lane == 0) {
+    t.digests[g] = (uint8_t)dg;
+    __stcg(reinterpret_cast<unsigned long long*>(t.scores + g), (unsigned long long)sc);
+  }
+  float* dst = value_ptr(t, g);
+  if (VEC16) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (uint32_t j = lane; j < (t.dim >> 2); j += 32) __stcg(d4 + j, __ldg(s4 + j));
+  } else {
+    for (uint32_t j = lane; j < t.dim; j += 32) __stcg(dst + j, __ldg(src + j));
+  }
+  __syncwarp();
+  if (lane == 0) publish_key(t.keys + g, key);
+  __syncwarp();
+}
+
 constexpr int kPrefetchAhead = 3;  // victim searches whose lines are prefetched ahead
 
 template <bool VEC16>
@@ -389,7 +448,8 @@ __global__ void __launch_bounds__(kInsThreads, 4)
   for (uint64_t c = warp; c < nchunks; c += nwarps) {
     // The chunk's 32 distinct keys: flags and miss records, coalesced.
     const uint64_t my_u = c * 32 + lane;
-    const bool miss = my_u < nu && s.mflag[my_u];
+    const uint8_t my_flag = my_u < nu ? s.mflag[my_u] : 0;
+    const bool miss = my_flag != 0;
     uint64_t my_key = 0;
     uint32_t my_i = 0, my_m = 0, my_e = 0;
     if (miss) {
@@ -408,7 +468,7 @@ __global__ void __launch_bounds__(kInsThreads, 4)
     // Phase A, one thread per key: claim a free slot of the less occupied
     // candidate (Algorithm 2 lines 6-9; Algorithm 3 phase D1). Keys whose
     // candidates are all full go on to the victim search.
-    bool pending = miss, full = false;
+    bool pending = my_flag == 1, full = my_flag == 2;
     for (int attempt = 0; __any_sync(kFull, pending) && attempt < kMaxClaimAttempts; ++attempt) {
       if (!pending) continue;
       if (attempt) claim_backoff(attempt, my_h);
