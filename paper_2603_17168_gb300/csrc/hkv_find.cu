@@ -16,7 +16,7 @@ namespace {
 constexpr int kFindThreads = 256;
 
 template <int G, bool VEC16, bool VALUES>
-__global__ void __launch_bounds__(kFindThreads)
+__global__ void __launch_bounds__(kFindThreads, 8)
     find_kernel(TableDev t, uint64_t n, const uint64_t* __restrict__ keys,
                 float* __restrict__ out, uint8_t* __restrict__ found,
                 uint64_t* __restrict__ scores_out, const OpDesc* __restrict__ d) {

@@ -424,7 +424,7 @@ __device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_
   __syncwarp();
 }
 
-constexpr int kPrefetchAhead = 3;  // victim searches whose lines are prefetched ahead
+constexpr int kPrefetchAhead = 1;  // victim searches whose lines are prefetched ahead
 
 template <bool VEC16>
 __global__ void __launch_bounds__(kInsThreads, 4)
@@ -508,8 +508,9 @@ __global__ void __launch_bounds__(kInsThreads, 4)
     }
 
     // Phase B, warp-cooperative victim search for the keys whose buckets
-    // were full. The score and key lines of the next searches are pulled
-    // into L2 by bulk prefetches while the current one runs.
+    // were full. The score and key lines of the next search are pulled
+    // into L2 by bulk prefetches while the current one runs (deeper
+    // prefetching measured slower: it competes for L2 and DRAM).
     unsigned todo = __ballot_sync(kFull, full);
     {
       unsigned ahead = todo;
