@@ -200,19 +200,27 @@ __device__ __forceinline__ void scan_free(const uint8_t* line, unsigned start, i
   uint4 v[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) v[q] = __ldcg(p + q);
+  const int s0 = (int)(start & 7);
+  int cand_hi = -1, cand_lo = -1;  // first free at/after the start piece, before it
   nfree = 0;
-  cand = -1;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int q = (k + start) & 7;
+  for (int q = 0; q < 8; ++q) {  // static indices: v stays in registers
     const uint32_t w[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const uint32_t z = __vcmpeq4(w[j], 0u);
       nfree += __popc(z) >> 3;
-      if (cand < 0 && z) cand = q * 16 + j * 4 + ((__ffs(z) - 1) >> 3);
+      if (z) {
+        const int c = q * 16 + j * 4 + ((__ffs(z) - 1) >> 3);
+        if (q >= s0) {
+          if (cand_hi < 0) cand_hi = c;
+        } else if (cand_lo < 0) {
+          cand_lo = c;
+        }
+      }
     }
   }
+  cand = cand_hi >= 0 ? cand_hi : cand_lo;
 }
 
 // One thread writes (digest, score, value) into a slot it holds LOCKED and
