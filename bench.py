@@ -219,11 +219,14 @@ def kernel_bytes(kind: str, c: dict, n_calls: int, batch: int, dim: int) -> floa
     u = c["unique"]
     uc = c.get("upd_claims", 0)
     if kind == "update":
-        # probe + in-place update of residents, and the free-slot claims made here
-        miss = u - c["updated"] - uc
-        return (u * (4 + S) + 128 * c["upd_lines"] + S * c["upd_keys"]
-                + c["updated"] * (2 * D + 2 * S + S) + miss * 4 * 4
-                + 128 * c.get("upd_claim_lines", 0) + uc * (3 * S + 2 * D + S))
+        # probe + in-place update of residents, and the free-slot claims made
+        # here: two occupancy counters read and one incremented, the key CAS,
+        # digest, score and status writes, the 32-B digest sectors scanned,
+        # the input row read and the value row written
+        deferred = u - c["updated"] - uc
+        return (u * (4 + 8 + 1 + S) + 128 * c["upd_lines"] + S * c["upd_keys"]
+                + c["updated"] * (2 * D + 2 * S + S) + deferred * 8
+                + S * c.get("upd_claim_lines", 0) + uc * (9 * S + 2 * D))
     if kind == "insert":
         ins = c["inserted"] - uc
         nm = ins + c["evicted"] + c["rejected"]

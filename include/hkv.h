@@ -227,7 +227,8 @@ enum {
   HKV_CNT_FIND_KEYS = 9,   /* full keys read by find / contains */
   HKV_CNT_UPD_LINES = 10,  /* digest lines read by the update phase */
   HKV_CNT_UPD_KEYS = 11,   /* full keys read by the update phase */
-  HKV_CNT_INS_LINES = 12,  /* digest lines read by the insert phase */
+  HKV_CNT_INS_LINES = 12,  /* digest lines read by the insert phase (0: free
+                              slots are claimed in the update phase) */
   HKV_CNT_INS_SCORES = 13, /* 1-KiB score lines read by victim searches */
   HKV_CNT_INS_KEYS = 14,   /* keys read by victim searches (tie-break) */
   HKV_CNT_TIMEOUT_FREE = 15,   /* free-slot claims that ran out of attempts */
@@ -239,7 +240,7 @@ enum {
   HKV_CNT_TIMEOUT_KEY = 18,    /* its key */
   HKV_CNT_UPD_CLAIMS = 19,     /* free-slot claims made by the update phase
                                   (included in HKV_CNT_INSERTED) */
-  HKV_CNT_UPD_CLAIM_LINES = 20, /* digest lines those claims read */
+  HKV_CNT_UPD_CLAIM_LINES = 20, /* 32-byte digest sectors those claims read */
   HKV_COUNTER_COUNT = 21
 };
 hkv_status hkv_read_counters(hkv_table_t t, uint64_t *out, hkv_stream_t stream);

@@ -4,6 +4,9 @@
 //   digests [B][128] uint8   one 128-byte line per bucket; 0 = empty slot
 //   keys    [B][128] uint64  2^64-1 = empty, 2^64-2 = locked (slot CAS lock)
 //   scores  [B][128] uint64  the eviction metadata itself (Sec. 3.3)
+//   sizes   [B] uint32       occupied (or claimed) slots per bucket: the
+//                            dual-bucket choice reads two counters instead
+//                            of counting 256 digests
 //   values  slices of (1 << slice_shift) slots x dim fp32, addressed by the
 //           global slot g = bucket * 128 + position; slice 0.. in HBM, the
 //           rest in pinned, mapped host memory (position-based addressing).
@@ -27,6 +30,7 @@ struct TableDev {
   uint8_t* digests;
   uint64_t* keys;
   uint64_t* scores;
+  uint32_t* sizes;           // [B] slots claimed per bucket
   float* values0;            // slice 0 base
   float* const* slices;      // [n_slices] slice bases (device array)
   uint64_t bucket_mask;      // B - 1
@@ -221,37 +225,115 @@ __device__ __forceinline__ void load_line(const uint8_t* line, int lane_g, uint3
   }
 }
 
+// The rest of a probe, for a lane whose share of the bucket held more
+// digest matches than the first pass recorded: walk the share again and
+// confirm every match other than c0..c2. Rare, so kept out of line (it
+// would otherwise hold registers across the common path).
+template <int G, bool CG>
+__device__ __noinline__ int probe_rest(const uint8_t* line, const uint64_t* kb, uint64_t key,
+                                       uint32_t pat4, int lane_g, int c0, int c1, int c2,
+                                       unsigned* key_reads) {
+  constexpr int W = 32 / G;
+  const int first = lane_g * (128 / G);
+  uint32_t w[W];
+  load_line<G, CG>(line, lane_g, w);
+  int my = -1;
+  unsigned reads = 0;
+#pragma unroll
+  for (int q = 0; q < W; ++q) {
+    uint32_t m = match4(w[q], pat4);
+    while (m) {
+      const int bit = __ffs(m) - 1;
+      const int slot = first + q * 4 + (bit >> 3);
+      m &= ~(0xFFu << (bit & ~7));
+      if (slot == c0 || slot == c1 || slot == c2) continue;
+      const uint64_t k = CG ? __ldcg(kb + slot) : __ldg(kb + slot);
+      reads++;
+      if (k == key) my = slot;
+    }
+  }
+  *key_reads += reads;
+  return my;
+}
+
 // Probe one bucket for `key` with a group of G lanes (G divides 32). Each
 // lane compares its 128/G digests and confirms matches against the full
 // key. Every lane of the warp must call this (it ends with a warp ballot).
 // Returns the slot (0..127) of the key in the bucket, or -1; identical on
 // all lanes of a group. Adds the full-key loads this lane made to key_reads.
-template <int G, bool CG>
+//
+// TWO_PASS: a lane waits on key memory once per bucket rather than once per
+// matching digest word: the first pass only records up to three digest
+// matches of the lane's share, whose key words are then loaded together. A
+// full bucket holds about 0.5 false matches per probe (128 digests of 255
+// values), so a lane whose three candidates were all false and whose share
+// held more (well under 1% of probes) re-walks the line for the rest. This
+// pays off in kernels with few warps per SM to hide latency (the update
+// phase); at full occupancy the one-pass form, which confirms each match as
+// it meets it, issues fewer instructions (find).
+template <int G, bool CG, bool TWO_PASS>
 __device__ __forceinline__ int probe_bucket(const TableDev& t, uint64_t b, uint64_t key,
                                             uint32_t pat4, bool active, int lane_g,
                                             unsigned group_bits, int group_base,
                                             unsigned& key_reads) {
+  constexpr int W = 32 / G;
   int my = -1;
-  if (active) {
-    uint32_t w[32 / G];
+  if (active && !TWO_PASS) {
+    uint32_t w[W];
     load_line<G, CG>(t.digests + b * kSlots, lane_g, w);
     const uint64_t* kb = t.keys + b * kSlots;
 #pragma unroll
-    for (int q = 0; q < 32 / G; ++q) {
+    for (int q = 0; q < W; ++q) {
       uint32_t m = match4(w[q], pat4);
       while (m) {
-        int bit = __ffs(m) - 1;
-        int slot = lane_g * (128 / G) + q * 4 + (bit >> 3);
-        uint64_t k = CG ? __ldcg(kb + slot) : __ldg(kb + slot);
+        const int bit = __ffs(m) - 1;
+        const int slot = lane_g * (128 / G) + q * 4 + (bit >> 3);
+        const uint64_t k = CG ? __ldcg(kb + slot) : __ldg(kb + slot);
         key_reads++;
         if (k == key) my = slot;
         m &= ~(0xFFu << (bit & ~7));
       }
     }
+  } else if (active) {
+    const uint8_t* line = t.digests + b * kSlots;
+    const uint64_t* kb = t.keys + b * kSlots;
+    const int first = lane_g * (128 / G);
+    int c0 = -1, c1 = -1, c2 = -1;
+    bool more = false;
+    auto push = [&](int slot) {
+      if (c0 < 0) c0 = slot;
+      else if (c1 < 0) c1 = slot;
+      else if (c2 < 0) c2 = slot;
+      else more = true;
+    };
+    {
+      uint32_t w[W];
+      load_line<G, CG>(line, lane_g, w);
+#pragma unroll
+      for (int q = 0; q < W; ++q) {
+        const uint32_t m = match4(w[q], pat4);
+        if (m) {  // 0xFF per matching byte: record the lowest and highest
+          const int sa = first + q * 4 + ((__ffs(m) - 1) >> 3);
+          const int sb = first + q * 4 + ((31 - __clz(m)) >> 3);
+          push(sa);
+          if (sb != sa) push(sb);
+          more |= __popc(m) > 16;
+        }
+      }
+    }
+    uint64_t k0 = 0, k1 = 0, k2 = 0;
+    if (c0 >= 0) k0 = CG ? __ldcg(kb + c0) : __ldg(kb + c0);
+    if (c1 >= 0) k1 = CG ? __ldcg(kb + c1) : __ldg(kb + c1);
+    if (c2 >= 0) k2 = CG ? __ldcg(kb + c2) : __ldg(kb + c2);
+    key_reads += (c0 >= 0) + (c1 >= 0) + (c2 >= 0);
+    if (c0 >= 0 && k0 == key) my = c0;
+    else if (c1 >= 0 && k1 == key) my = c1;
+    else if (c2 >= 0 && k2 == key) my = c2;
+    else if (more) my = probe_rest<G, CG>(line, kb, key, pat4, lane_g, c0, c1, c2, &key_reads);
   }
-  unsigned bal = __ballot_sync(0xFFFFFFFFu, my >= 0) & group_bits;
-  int src = bal ? __ffs(bal) - 1 : group_base;
-  int slot = __shfl_sync(0xFFFFFFFFu, my, src);
+  const unsigned bal = __ballot_sync(0xFFFFFFFFu, my >= 0) & group_bits;
+  const int src = bal ? __ffs(bal) - 1 : group_base;
+  const int slot = __shfl_sync(0xFFFFFFFFu, my, src);
   return bal ? slot : -1;
 }
 

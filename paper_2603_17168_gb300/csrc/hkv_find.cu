@@ -43,16 +43,16 @@ __global__ void __launch_bounds__(kFindThreads, 8)
     uint64_t h = fmix64(key);
     uint64_t b = h & t.bucket_mask;
     uint32_t pat4 = digest_from_hash(h) * 0x01010101u;
-    int slot = probe_bucket<G, false>(t, b, key, pat4, active, lane_g, group_bits, group_base,
-                                      kreads);
+    int slot = probe_bucket<G, false, false>(t, b, key, pat4, active, lane_g, group_bits,
+                                             group_base, kreads);
     lines += active && lane_g == 0;
     if (t.dual) {
       uint64_t b2 = second_bucket(t, key);
       bool need = active && slot < 0 && b2 != b;
       lines += need && lane_g == 0;
       if (__any_sync(0xFFFFFFFFu, need)) {
-        int s2 = probe_bucket<G, false>(t, b2, key, pat4, need, lane_g, group_bits, group_base,
-                                        kreads);
+        int s2 = probe_bucket<G, false, false>(t, b2, key, pat4, need, lane_g, group_bits,
+                                               group_base, kreads);
         if (need && s2 >= 0) {
           slot = s2;
           b = b2;

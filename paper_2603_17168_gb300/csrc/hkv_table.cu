@@ -179,10 +179,11 @@ hkv_status hkv_create(const hkv_options* o, hkv_table_t* out) {
   const uint64_t slots = t->capacity;
   const uint64_t dim = o->dim;
 
-  // metadata: digests | keys | scores | err | counters
+  // metadata: digests | keys | scores | sizes | err | counters
   const uint64_t off_keys = slots;                    // digests: slots bytes (multiple of 128)
   const uint64_t off_scores = off_keys + slots * 8;
-  const uint64_t off_err = off_scores + slots * 8;
+  const uint64_t off_sizes = off_scores + slots * 8;
+  const uint64_t off_err = off_sizes + ((nb * 4 + 255) & ~255ull);
   const uint64_t off_cnt = off_err + 256;
   const uint64_t meta_bytes = off_cnt + 256;
   cudaError_t e = cudaMalloc(&t->meta, meta_bytes);
@@ -194,6 +195,7 @@ hkv_status hkv_create(const hkv_options* o, hkv_table_t* out) {
   t->dev.digests = reinterpret_cast<uint8_t*>(m);
   t->dev.keys = reinterpret_cast<uint64_t*>(m + off_keys);
   t->dev.scores = reinterpret_cast<uint64_t*>(m + off_scores);
+  t->dev.sizes = reinterpret_cast<uint32_t*>(m + off_sizes);
   t->dev.err = reinterpret_cast<uint32_t*>(m + off_err);
   t->dev.counters = reinterpret_cast<unsigned long long*>(m + off_cnt);
   t->dev.bucket_mask = nb - 1;
@@ -265,13 +267,14 @@ hkv_status hkv_create(const hkv_options* o, hkv_table_t* out) {
 
   init_meta_kernel<<<std::max(1, t->num_sms * 8), 256>>>(t->dev.digests, t->dev.keys,
                                                          t->dev.scores, slots);
+  cudaMemset(t->dev.sizes, 0, nb * 4);
   cudaMemset(t->dev.err, 0, 256);
   cudaMemset(t->dev.counters, 0, 256);
   // Default launch shape (the autotuner refines it per table): few threads
   // per key keep the probe kernels from being issue-bound; wide values get
   // more lanes for the row copy.
   t->launch.find_tpk = t->opts.dim <= 32 ? 2 : (t->opts.dim <= 128 ? 4 : 8);
-  t->launch.update_tpk = t->opts.dim <= 32 ? 1 : (t->opts.dim <= 128 ? 2 : 4);
+  t->launch.update_tpk = t->opts.dim <= 128 ? 2 : 4;
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     free_table(t);

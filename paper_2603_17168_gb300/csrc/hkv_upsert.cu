@@ -8,16 +8,17 @@
 //             atomic per block instead of one per occurrence. The distinct
 //             keys get dense indices u (one list reservation per block);
 //   update    phase U: probe every distinct key (G lanes per key, digest
-//             line + key confirm) and update residents in place; a miss
-//             leaves (key, source row, multiplicity) at its index u;
-//   insert    phase I: a warp takes 32 consecutive u. Each thread claims
-//             a free slot for its own miss with a CAS on the key word
-//             (EMPTY -> LOCKED); keys whose bucket (both buckets in dual
-//             mode) is full then get a warp-cooperative victim search that
-//             reduces the minimum (score, key) over the 128 (256) slots,
-//             applies admission control, CAS-locks the victim and replaces
-//             it (Algorithm 2 lines 6-14, Algorithm 3). The next searches'
-//             score and key lines are bulk-prefetched into L2;
+//             line + key confirm) and update residents in place. A miss
+//             claims a free slot of the less occupied candidate bucket
+//             (per-bucket occupancy counters, a CAS on the key word
+//             EMPTY -> LOCKED); a miss whose buckets are all full is left
+//             at its index u for phase I;
+//   insert    phase I: a warp takes 32 consecutive u and runs a
+//             warp-cooperative victim search for each full-bucket miss: the
+//             minimum (score, key) over the 128 (256) slots, admission
+//             control, a CAS lock on the victim, replacement (Algorithm 2
+//             lines 6-14, Algorithm 3). The next search's score and key
+//             lines are bulk-prefetched into L2;
 //   reconcile a victim that was itself inserted by this batch is not an
 //             eviction: its key becomes REJECTED and it is dropped from the
 //             evicted output, which is compacted here;
@@ -57,7 +58,7 @@ struct Scratch {
   uint32_t* slot_of;         // [n] dedup entry of each batch position
   uint32_t* ulist;           // [n] dedup entry of distinct key u
   uint8_t* mflag;            // [n] 1 if distinct key u missed in phase U
-  uint64_t* mkey;            // [n] key u (misses)
+  uint64_t* mkey;            // [n] key u (written by dedup for every distinct key)
   uint32_t* mi;              // [n] batch index of its last occurrence (misses)
   uint32_t* mm;              // [n] its multiplicity (misses)
   unsigned long long* cnt;   // [kCntWords]
@@ -167,7 +168,11 @@ __global__ void __launch_bounds__(kDedupThreads)
   unsigned long long u = block_reserve(s.cnt + kCntUnique, nfirst);
 #pragma unroll
   for (int q = 0; q < kDedupPerThread; ++q)
-    if (firsts & (1u << q)) s.ulist[u++] = gps[q];
+    if (firsts & (1u << q)) {
+      s.ulist[u] = gps[q];
+      s.mkey[u] = sm[threadIdx.x + q * kDedupThreads].key;
+      ++u;
+    }
 #pragma unroll
   for (int j = 0; j < kDedupKPT; ++j) {
     if (pos[j] < 0) continue;
@@ -192,40 +197,45 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* p, unsigned bytes) 
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Free slots of a bucket as seen by one thread: count, and one candidate
-// found by scanning the 16-byte pieces of the digest line from a
-// key-dependent start (so keys of one bucket rarely pick the same slot).
-__device__ __forceinline__ void scan_free(const uint8_t* line, unsigned start, int& nfree, int& cand) {
+// Slot of the first free digest (0) in a 16-slot piece of a digest line,
+// or -1.
+__device__ __forceinline__ int free_in_piece(const uint4& v) {
+  const uint32_t z[4] = {__vcmpeq4(v.x, 0u), __vcmpeq4(v.y, 0u), __vcmpeq4(v.z, 0u),
+                         __vcmpeq4(v.w, 0u)};
+  int slot = -1;
+#pragma unroll
+  for (int j = 3; j >= 0; --j)
+    if (z[j]) slot = j * 4 + ((__ffs(z[j]) - 1) >> 3);
+  return slot;
+}
+
+// A free slot of a bucket, scanning its digest line through L2 two pieces
+// (32 slots, one sector) per round trip from a key-dependent start, so that
+// keys claiming in one bucket rarely race for the same slot. -1 if the line
+// shows no free slot. `sectors` counts the 32-byte reads.
+__device__ __forceinline__ int find_free(const uint8_t* line, unsigned start, unsigned& sectors) {
   const uint4* p = reinterpret_cast<const uint4*>(line);
-  uint4 v[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = __ldcg(p + q);
-  const int s0 = (int)(start & 7);
-  int cand_hi = -1, cand_lo = -1;  // first free at/after the start piece, before it
-  nfree = 0;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {  // static indices: v stays in registers
-    const uint32_t w[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t z = __vcmpeq4(w[j], 0u);
-      nfree += __popc(z) >> 3;
-      if (z) {
-        const int c = q * 16 + j * 4 + ((__ffs(z) - 1) >> 3);
-        if (q >= s0) {
-          if (cand_hi < 0) cand_hi = c;
-        } else if (cand_lo < 0) {
-          cand_lo = c;
-        }
-      }
-    }
+#pragma unroll 1
+  for (int r = 0; r < 4; ++r) {
+    const unsigned q0 = (start + 2 * r) & 6;  // sector-aligned pair of pieces
+    const uint4 a = __ldcg(p + q0), b = __ldcg(p + q0 + 1);
+    sectors++;
+    int s = free_in_piece(a);
+    if (s >= 0) return (int)q0 * 16 + s;
+    s = free_in_piece(b);
+    if (s >= 0) return (int)(q0 + 1) * 16 + s;
   }
-  cand = cand_hi >= 0 ? cand_hi : cand_lo;
+  return -1;
 }
 
 // One thread writes (digest, score, value) into a slot it holds LOCKED and
-// publishes the key with a release store (digest first: see fill_slot).
-template <bool VEC16>
+// publishes the key (digest first: see fill_slot). RELEASE orders the
+// digest, score and value stores before the key for readers in the same
+// kernel that act on a published key's score or value (victim searches).
+// Phase U has no such reader (no eviction runs beside it, probes of other
+// keys never match this key) and the kernel boundary orders everything for
+// the next phase, so its claims publish with a plain store.
+template <bool VEC16, bool RELEASE>
 __device__ __forceinline__ void fill_slot_thread(const TableDev& t, uint64_t g, uint64_t key,
                                                  uint64_t sc, uint32_t dg, const float* src) {
   t.digests[g] = (uint8_t)dg;
@@ -238,7 +248,10 @@ __device__ __forceinline__ void fill_slot_thread(const TableDev& t, uint64_t g, 
   } else {
     for (uint32_t j = 0; j < t.dim; ++j) __stcg(dst + j, __ldg(src + j));
   }
-  publish_key(t.keys + g, key);
+  if (RELEASE)
+    publish_key(t.keys + g, key);
+  else
+    __stcg(reinterpret_cast<unsigned long long*>(t.keys + g), (unsigned long long)key);
 }
 
 // Back-off before retry `attempt` (> 0): exponential up to ~16 us, with
@@ -249,38 +262,42 @@ __device__ __forceinline__ void claim_backoff(int attempt, uint64_t h) {
   __nanosleep(base + ((unsigned)(h >> 17) & 255u));
 }
 
-// Phase I's free-slot claim for one key, run by one thread (Algorithm 2
+// Free-slot claim for one missing key, run by one thread (Algorithm 2
 // lines 6-9; Algorithm 3 phase D1: a free slot of the less occupied
-// candidate, b1 on equal occupancy). Returns 0 when the key was placed (or
-// the bounded wait ran out and the error was latched), 2 when every
-// candidate bucket is full and the key needs a victim search.
+// candidate bucket, b1 on equal occupancy). Occupancy comes from the
+// per-bucket counters, which count a slot from the moment its claim CAS
+// succeeds, so a counter never exceeds the slots really taken: a counter at
+// 128 means full, and a bucket whose counter lags behind its digests is
+// simply scanned again. Returns 0 when the key was placed (or the bounded
+// wait ran out and the error was latched), 2 when every candidate bucket
+// is full and the key needs a victim search.
 template <bool VEC16>
 __device__ __forceinline__ uint8_t claim_free_slot(const TableDev& t, const Scratch& s, uint32_t e,
                                                    uint64_t key, uint64_t h, uint64_t sc,
-                                                   const float* src, unsigned& lines,
+                                                   const float* src, unsigned& sectors,
                                                    unsigned& inserted, unsigned& retries) {
   const uint64_t b1 = h & t.bucket_mask;
   const uint64_t b2 = t.dual ? second_bucket(t, key) : b1;
   const bool two = b2 != b1;
   for (int attempt = 0; attempt < kMaxClaimAttempts; ++attempt) {
     if (attempt) claim_backoff(attempt, h);
-    const unsigned start = (unsigned)(h >> 40) + (unsigned)attempt;
-    int f1, c1, f2 = 0, c2 = -1;
-    scan_free(t.digests + b1 * kSlots, start, f1, c1);
-    lines++;
-    if (two) {
-      scan_free(t.digests + b2 * kSlots, start, f2, c2);
-      lines++;
+    const uint32_t n1 = __ldcg(t.sizes + b1);
+    const uint32_t n2 = two ? __ldcg(t.sizes + b2) : kSlots;
+    if (n1 >= kSlots && n2 >= kSlots) return 2;
+    const uint64_t b = n1 <= n2 ? b1 : b2;
+    const int slot = find_free(t.digests + b * kSlots, (unsigned)(h >> 40) + 2u * attempt, sectors);
+    if (slot < 0) {
+      retries++;
+      continue;
     }
-    if (f1 == 0 && f2 == 0) return 2;
-    const bool use1 = !two || f1 >= f2;
-    const uint64_t g = (use1 ? b1 : b2) * kSlots + (uint64_t)(use1 ? c1 : c2);
+    const uint64_t g = b * kSlots + (uint64_t)slot;
     if (atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + g), kEmptyKey, kLockedKey) !=
         kEmptyKey) {
       retries++;
       continue;
     }
-    fill_slot_thread<VEC16>(t, g, key, sc, digest_from_hash(h), src);
+    atomicAdd(t.sizes + b, 1u);
+    fill_slot_thread<VEC16, false>(t, g, key, sc, digest_from_hash(h), src);
     s.tstatus[e] = HKV_ST_INSERTED;
     inserted++;
     return 0;
@@ -295,10 +312,38 @@ __device__ __forceinline__ uint8_t claim_free_slot(const TableDev& t, const Scra
 
 // ----------------------------------------------------------- phase U probe
 
+// New score of a resident key (the hit branch of the table policy) written
+// with the fewest memory round trips: LRU-type and caller scores are plain
+// stores, LFU is an add whose result nobody waits for (an LFU score is a sum
+// of batch multiplicities, so it never reaches the saturation point 2^64 - 1
+// and the saturating add is a plain add), CUSTOM without caller scores keeps
+// the score; the saturating sub-field counters read the old score first.
+__device__ __forceinline__ void update_resident_score(const TableDev& t, uint64_t g, uint64_t m,
+                                                      bool have_caller, uint64_t caller,
+                                                      const ScoreCtx& c) {
+  unsigned long long* p = reinterpret_cast<unsigned long long*>(t.scores + g);
+  switch (t.policy) {
+    case HKV_LFU:
+      atomicAdd(p, (unsigned long long)m);
+      return;
+    case HKV_LRU:
+    case HKV_EPOCH_LRU:
+      *p = policy_score(t.policy, true, 0, m, have_caller, caller, c);
+      return;
+    case HKV_CUSTOM:
+      if (have_caller) *p = caller;
+      return;
+    default:
+      *p = policy_score(t.policy, true, *p, m, have_caller, caller, c);
+  }
+}
+
+
 constexpr int kUpdThreads = 256;
+constexpr int kUpdBlocksPerSm = 4;  // resident blocks per SM (register bound)
 
 template <int G, bool VEC16, bool UPSERT>
-__global__ void __launch_bounds__(kUpdThreads, 4)
+__global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
     update_kernel(TableDev t, Scratch s, const float* __restrict__ values,
                   const uint64_t* __restrict__ scores_in, ScoreCtx ctx) {
   if (aborted(s)) return;
@@ -321,21 +366,32 @@ __global__ void __launch_bounds__(kUpdThreads, 4)
   for (uint64_t base = warp * KPW; base < nu; base += nwarps * KPW) {
     const uint64_t u = base + (lane / G);
     const bool active = u < nu;
-    const uint32_t e = active ? s.ulist[u] : 0;
-    const uint64_t key = active ? s.tab[e].key : kEmptyKey;
+    // The distinct key comes from the dense list dedup wrote (no load
+    // dependent on its dedup entry); the entry's (last index, count) word
+    // is fetched beside it.
+    uint32_t e = 0;
+    uint64_t key = kEmptyKey;
+    uint2 nc = make_uint2(0u, 0u);
+    if (active) {
+      e = __ldg(s.ulist + u);
+      key = __ldg(s.mkey + u);
+      nc = __ldg(reinterpret_cast<const uint2*>(s.tab + e) + 1);
+    }
+    const uint64_t i = (uint32_t)~nc.x;
+    const uint64_t m = (uint64_t)nc.y + 1;
     const uint64_t h = fmix64(key);
     uint64_t b = h & t.bucket_mask;
     const uint32_t pat4 = digest_from_hash(h) * 0x01010101u;
-    int slot = probe_bucket<G, false>(t, b, key, pat4, active, lane_g, group_bits, group_base,
-                                      kreads);
+    int slot = probe_bucket<G, false, true>(t, b, key, pat4, active, lane_g, group_bits,
+                                            group_base, kreads);
     lines += active && lane_g == 0;
     if (t.dual) {
       const uint64_t b2 = second_bucket(t, key);
       const bool need = active && slot < 0 && b2 != b;
       lines += need && lane_g == 0;
       if (__any_sync(kFull, need)) {
-        const int s2 = probe_bucket<G, false>(t, b2, key, pat4, need, lane_g, group_bits,
-                                              group_base, kreads);
+        const int s2 = probe_bucket<G, false, true>(t, b2, key, pat4, need, lane_g, group_bits,
+                                                    group_base, kreads);
         if (need && s2 >= 0) {
           slot = s2;
           b = b2;
@@ -344,37 +400,31 @@ __global__ void __launch_bounds__(kUpdThreads, 4)
     }
     const bool hit = active && slot >= 0;
     if (active) {
-      const uint64_t i = ~s.tab[e].nlast;
-      const uint64_t m = (uint64_t)s.tab[e].cnt_m1 + 1;
       if (hit) {
         const uint64_t g = b * kSlots + (uint64_t)slot;
         if (values) copy_row<G, VEC16, false>(value_ptr(t, g), values + i * t.dim, t.dim, lane_g);
         if (lane_g == 0) {
-          const uint64_t old = t.scores[g];
-          t.scores[g] = policy_score(t.policy, true, old, m, scores_in != nullptr,
-                                     scores_in ? __ldg(scores_in + i) : 0, ctx);
+          update_resident_score(t, g, m, scores_in != nullptr, scores_in ? __ldg(scores_in + i) : 0,
+                                ctx);
           s.tstatus[e] = HKV_ST_UPDATED;
           updated++;
         }
       }
       if (UPSERT && lane_g == 0) {
-        // mflag: 0 placed (updated, or claimed here), 1 miss left to the
-        // insert kernel, 2 miss whose candidate buckets are all full
-        uint8_t flag = hit ? 0 : 1;
-        if constexpr (G == 1) {
-          // A miss claims its free slot right here: a claim into an empty
-          // slot cannot race the in-place updates of this phase (they
-          // touch other slots), only evictions must wait for phase U.
-          if (!hit) {
-            const uint64_t sc = policy_score(t.policy, false, 0, m, scores_in != nullptr,
-                                             scores_in ? __ldg(scores_in + i) : 0, ctx);
-            flag = claim_free_slot<VEC16>(t, s, e, key, h, sc, values + i * t.dim, ins_lines,
-                                          inserted, retries);
-          }
+        // mflag: 0 placed (updated, or claimed here), 2 miss whose
+        // candidate buckets are all full. A miss claims its free slot right
+        // here: a claim into an empty slot cannot race the in-place updates
+        // of this phase (they touch other slots); only evictions must wait
+        // for phase U to end.
+        uint8_t flag = 0;
+        if (!hit) {
+          const uint64_t sc = policy_score(t.policy, false, 0, m, scores_in != nullptr,
+                                           scores_in ? __ldg(scores_in + i) : 0, ctx);
+          flag = claim_free_slot<VEC16>(t, s, e, key, h, sc, values + i * t.dim, ins_lines,
+                                        inserted, retries);
         }
         s.mflag[u] = flag;
         if (flag) {
-          s.mkey[u] = key;
           s.mi[u] = (uint32_t)i;
           s.mm[u] = (uint32_t)m;
         }
@@ -451,7 +501,7 @@ __global__ void __launch_bounds__(kInsThreads, 4)
   const uint64_t nu = s.cnt[kCntUnique];
   const uint64_t nchunks = (nu + 31) / 32;
   unsigned inserted = 0, evicted = 0, rejected = 0, retries = 0;
-  unsigned lines = 0, score_lines = 0, kreads = 0;
+  unsigned score_lines = 0, kreads = 0;
 
   for (uint64_t c = warp; c < nchunks; c += nwarps) {
     // The chunk's 32 distinct keys: flags and miss records, coalesced.
@@ -473,52 +523,15 @@ __global__ void __launch_bounds__(kInsThreads, 4)
     const uint64_t my_sc = policy_score(t.policy, false, 0, my_m, scores_in != nullptr,
                                         (miss && scores_in) ? __ldg(scores_in + my_i) : 0, ctx);
 
-    // Phase A, one thread per key: claim a free slot of the less occupied
-    // candidate (Algorithm 2 lines 6-9; Algorithm 3 phase D1). Keys whose
-    // candidates are all full go on to the victim search.
-    bool pending = my_flag == 1, full = my_flag == 2;
-    for (int attempt = 0; __any_sync(kFull, pending) && attempt < kMaxClaimAttempts; ++attempt) {
-      if (!pending) continue;
-      if (attempt) claim_backoff(attempt, my_h);
-      const unsigned start = (unsigned)(my_h >> 40) + (unsigned)attempt;
-      int f1, c1, f2 = 0, c2 = -1;
-      scan_free(t.digests + my_b1 * kSlots, start, f1, c1);
-      lines++;
-      if (my_two) {
-        scan_free(t.digests + my_b2 * kSlots, start, f2, c2);
-        lines++;
-      }
-      if (f1 == 0 && f2 == 0) {
-        pending = false;
-        full = true;
-        continue;
-      }
-      const bool use1 = !my_two || f1 >= f2;
-      const uint64_t g = (use1 ? my_b1 : my_b2) * kSlots + (uint64_t)(use1 ? c1 : c2);
-      if (atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + g), kEmptyKey, kLockedKey) !=
-          kEmptyKey) {
-        retries++;
-        continue;
-      }
-      fill_slot_thread<VEC16>(t, g, my_key, my_sc, digest_from_hash(my_h), values + my_i * t.dim);
-      pending = false;
-      inserted++;
-      s.evk[my_u] = kEmptyKey;
-      s.tstatus[my_e] = HKV_ST_INSERTED;
-    }
-    if (pending) {  // bounded wait ran out
-      latch_error(t.err, HKV_ERR_TIMEOUT);
-      atomicAdd(t.counters + HKV_CNT_TIMEOUT_FREE, 1ull);
-      atomicExch(t.counters + HKV_CNT_TIMEOUT_WHY, 5ull);
-      atomicExch(t.counters + HKV_CNT_TIMEOUT_KEY, (unsigned long long)my_key);
-      s.evk[my_u] = kEmptyKey;
-      s.tstatus[my_e] = HKV_ST_REJECTED;
-    }
+    // Misses with a free slot were placed by the update phase; what is
+    // left (mflag 2) found every candidate bucket full.
+    const bool full = my_flag == 2;
 
-    // Phase B, warp-cooperative victim search for the keys whose buckets
-    // were full. The score and key lines of the next search are pulled
-    // into L2 by bulk prefetches while the current one runs (deeper
-    // prefetching measured slower: it competes for L2 and DRAM).
+    // Warp-cooperative victim search for the keys whose buckets were
+    // full, one key after another. The score and key lines of the next
+    // search are pulled into L2 by bulk prefetches while the current one
+    // runs (deeper prefetching measured slower: it competes for L2 and
+    // DRAM).
     unsigned todo = __ballot_sync(kFull, full);
     {
       unsigned ahead = todo;
@@ -679,7 +692,7 @@ __global__ void __launch_bounds__(kInsThreads, 4)
   const int which[7] = {HKV_CNT_INSERTED, HKV_CNT_EVICTED, HKV_CNT_REJECTED, HKV_CNT_RETRIES,
                         HKV_CNT_INS_LINES, HKV_CNT_INS_SCORES, HKV_CNT_INS_KEYS};
   const unsigned vals[7] = {inserted, lane == 0 ? evicted : 0u, lane == 0 ? rejected : 0u,
-                            retries, lines, lane == 0 ? score_lines : 0u, kreads};
+                            retries, 0u, lane == 0 ? score_lines : 0u, kreads};
   flush_counts(t, which, vals);
 }
 
@@ -769,22 +782,26 @@ __global__ void __launch_bounds__(kUpdThreads)
     const uint32_t pat4 = digest_from_hash(h) * 0x01010101u;
     // Duplicates in the batch may clear the slot concurrently: read through L2.
     unsigned kreads = 0;
-    int slot = probe_bucket<G, true>(t, b, key, pat4, active, lane_g, group_bits, group_base,
-                                     kreads);
+    int slot = probe_bucket<G, true, false>(t, b, key, pat4, active, lane_g, group_bits,
+                                            group_base, kreads);
     if (t.dual) {
       const uint64_t b2 = second_bucket(t, key);
       const bool need = active && slot < 0 && b2 != b;
       if (__any_sync(kFull, need)) {
-        const int s2 = probe_bucket<G, true>(t, b2, key, pat4, need, lane_g, group_bits,
-                                             group_base, kreads);
+        const int s2 = probe_bucket<G, true, false>(t, b2, key, pat4, need, lane_g,
+                                                    group_bits, group_base, kreads);
         if (need && s2 >= 0) { slot = s2; b = b2; }
       }
     }
     if (active && slot >= 0 && lane_g == 0) {
       const uint64_t g = b * kSlots + (uint64_t)slot;
-      t.digests[g] = 0;
-      t.keys[g] = kEmptyKey;
-      t.scores[g] = 0;
+      // Duplicates of a key in one erase batch all find its slot: the CAS
+      // lets exactly one of them clear it and count it out of its bucket.
+      if (atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + g), key, kEmptyKey) == key) {
+        t.digests[g] = 0;
+        t.scores[g] = 0;
+        atomicSub(t.sizes + b, 1u);
+      }
     }
   }
 }
@@ -810,8 +827,8 @@ hkv_status alloc_scratch(hkv_table_s* t, uint64_t n, bool upsert, bool want_ev_v
   const uint64_t sz_u64 = align256(n * 8);
   const uint64_t sz_cnt = align256(kCntWords * 8);
   const uint64_t sz_evv = want_ev_values ? align256(n * (uint64_t)t->dev.dim * 4) : 0;
-  uint64_t total = sz_tab + sz_ts + 2 * sz_u32 + sz_cnt;
-  if (upsert) total += sz_u8 + 3 * sz_u64 + 2 * sz_u32 + sz_evv;
+  uint64_t total = sz_tab + sz_ts + 2 * sz_u32 + sz_cnt + sz_u64;
+  if (upsert) total += sz_u8 + 2 * sz_u64 + 2 * sz_u32 + sz_evv;
   cudaError_t e = cudaMallocFromPoolAsync(&a->base, total, t->pool, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -827,9 +844,9 @@ hkv_status alloc_scratch(hkv_table_s* t, uint64_t n, bool upsert, bool want_ev_v
   s.slot_of = reinterpret_cast<uint32_t*>(p); p += sz_u32;
   s.ulist = reinterpret_cast<uint32_t*>(p); p += sz_u32;
   s.cnt = reinterpret_cast<unsigned long long*>(p); p += sz_cnt;
+  s.mkey = reinterpret_cast<uint64_t*>(p); p += sz_u64;
   if (upsert) {
     s.mflag = reinterpret_cast<uint8_t*>(p); p += sz_u8;
-    s.mkey = reinterpret_cast<uint64_t*>(p); p += sz_u64;
     s.evk = reinterpret_cast<uint64_t*>(p); p += sz_u64;
     s.evs = reinterpret_cast<uint64_t*>(p); p += sz_u64;
     s.mi = reinterpret_cast<uint32_t*>(p); p += sz_u32;
@@ -851,7 +868,10 @@ unsigned grid_for(const hkv_table_s* t, uint64_t threads_needed, int block, int 
 template <int G, bool UPSERT>
 void launch_update_g(hkv_table_s* t, uint64_t n, const Scratch& s, const float* values,
                      const uint64_t* scores, ScoreCtx ctx, bool vec16, cudaStream_t st) {
-  const unsigned grid = grid_for(t, n * G, kUpdThreads, 2048 / kUpdThreads);
+  // Two waves of resident blocks: a block whose warps finish early hands
+  // its slot to a waiting block instead of idling at the closing barrier
+  // (measured faster than one wave of longer-running blocks).
+  const unsigned grid = grid_for(t, n * G, kUpdThreads, 2 * kUpdBlocksPerSm);
   KernelTimer timer(t->prof, HKV_K_UPDATE, st);
   if (vec16)
     update_kernel<G, true, UPSERT><<<grid, kUpdThreads, 0, st>>>(t->dev, s, values, scores, ctx);
