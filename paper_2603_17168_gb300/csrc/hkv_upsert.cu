@@ -114,12 +114,18 @@ __global__ void __launch_bounds__(kDedupThreads)
   __syncthreads();
   const uint64_t tile0 = (uint64_t)blockIdx.x * kDedupTile;
   int pos[kDedupKPT];
+  uint64_t kin[kDedupKPT];  // all of the tile's loads in flight at once
+#pragma unroll
+  for (int j = 0; j < kDedupKPT; ++j) {
+    const uint64_t idx = tile0 + (uint64_t)j * kDedupThreads + threadIdx.x;
+    kin[j] = idx < n ? __ldg(keys + idx) : 0;
+  }
 #pragma unroll
   for (int j = 0; j < kDedupKPT; ++j) {
     pos[j] = -1;
     const uint64_t idx = tile0 + (uint64_t)j * kDedupThreads + threadIdx.x;
     if (idx >= n) continue;
-    const uint64_t k = __ldg(keys + idx);
+    const uint64_t k = kin[j];
     if (k >= kFirstReserved) {
       abort_batch(s, t.err, HKV_ERR_RESERVED_KEY);
       continue;
@@ -135,32 +141,43 @@ __global__ void __launch_bounds__(kDedupThreads)
     pos[j] = (int)p;
   }
   __syncthreads();
-  // Merge this tile's distinct keys into the global table.
+  // Merge this tile's distinct keys into the global table. A thread's
+  // entries go four at a time: their first CAS attempts are issued together
+  // (independent addresses), and only collisions walk on one by one.
   uint32_t gps[kDedupPerThread];
   unsigned nfirst = 0, firsts = 0;
 #pragma unroll
-  for (int q = 0; q < kDedupPerThread; ++q) {
-    const int p = threadIdx.x + q * kDedupThreads;
-    gps[q] = 0;
-    const unsigned long long k = sm[p].key;
-    if (k == kEmptyKey) continue;
-    const uint32_t c = sm[p].cnt_m1 + 1u;
-    uint64_t gp = dedup_pos(k, tab_bits);
-    bool first = false;
-    for (;;) {  // the table holds >= 2n entries: terminates
-      const unsigned long long old = atomicCAS(&s.tab[gp].key, kEmptyKey, k);
-      if (old == kEmptyKey) { first = true; break; }
-      if (old == k) break;
-      gp = (gp + 1) & tab_mask;
+  for (int h = 0; h < kDedupPerThread; h += 4) {
+    unsigned long long kq[4], old[4];
+    uint64_t gq[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      kq[j] = sm[threadIdx.x + (h + j) * kDedupThreads].key;
+      gq[j] = dedup_pos(kq[j], tab_bits);
+      old[j] = kq[j] != kEmptyKey ? atomicCAS(&s.tab[gq[j]].key, kEmptyKey, kq[j]) : 0ull;
     }
-    atomicMin(&s.tab[gp].nlast, sm[p].nlast);
-    atomicAdd(&s.tab[gp].cnt_m1, c);
-    if (deterministic && (!first || c > 1)) abort_batch(s, t.err, HKV_ERR_DUPLICATE_KEY);
-    gps[q] = (uint32_t)gp;
-    sm[p].cnt_m1 = (uint32_t)gp;  // reuse: global entry of this key
-    if (first) {
-      firsts |= 1u << q;
-      nfirst++;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = h + j;
+      const int p = threadIdx.x + q * kDedupThreads;
+      gps[q] = 0;
+      if (kq[j] == kEmptyKey) continue;
+      // the table holds >= 2n entries: terminates
+      while (old[j] != kEmptyKey && old[j] != kq[j]) {
+        gq[j] = (gq[j] + 1) & tab_mask;
+        old[j] = atomicCAS(&s.tab[gq[j]].key, kEmptyKey, kq[j]);
+      }
+      const bool first = old[j] == kEmptyKey;
+      const uint32_t c = sm[p].cnt_m1 + 1u;
+      atomicMin(&s.tab[gq[j]].nlast, sm[p].nlast);
+      atomicAdd(&s.tab[gq[j]].cnt_m1, c);
+      if (deterministic && (!first || c > 1)) abort_batch(s, t.err, HKV_ERR_DUPLICATE_KEY);
+      gps[q] = (uint32_t)gq[j];
+      sm[p].cnt_m1 = (uint32_t)gq[j];  // reuse: global entry of this key
+      if (first) {
+        firsts |= 1u << q;
+        nfirst++;
+      }
     }
   }
   // One list reservation per block for the keys this block saw first
@@ -440,14 +457,32 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
 // --------------------------------------------------------- phase I insert
 
 constexpr int kInsThreads = 256;
+constexpr int kInsBlocksPerSm = 4;  // resident blocks per SM (register bound)
 
-__device__ __forceinline__ unsigned long long shfl_min_u64(unsigned long long v) {
+// Warp minimum of a 64-bit value as two 32-bit min-reductions (redux.sync).
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+  const uint32_t hi = __reduce_min_sync(kFull, (uint32_t)(v >> 32));
+  const uint32_t lo = __reduce_min_sync(kFull, (uint32_t)(v >> 32) == hi ? (uint32_t)v : ~0u);
+  return ((unsigned long long)hi << 32) | lo;
+}
+
+// Warp-wide lexicographic minimum of the lanes' (s, k) pairs as four 32-bit
+// min-reductions, most significant word first, each over the lanes still
+// tied; `mine` is set on the lanes holding the minimum pair.
+__device__ __forceinline__ void warp_min_sk(unsigned long long s, unsigned long long k,
+                                            unsigned long long& smin, unsigned long long& kmin,
+                                            bool& mine) {
+  const uint32_t w[4] = {(uint32_t)(s >> 32), (uint32_t)s, (uint32_t)(k >> 32), (uint32_t)k};
+  uint32_t m[4];
+  bool tied = true;
 #pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    const unsigned long long w = __shfl_xor_sync(kFull, v, o);
-    v = w < v ? w : v;
+  for (int j = 0; j < 4; ++j) {
+    m[j] = __reduce_min_sync(kFull, tied ? w[j] : ~0u);
+    tied = tied && w[j] == m[j];
   }
-  return v;
+  smin = ((unsigned long long)m[0] << 32) | m[1];
+  kmin = ((unsigned long long)m[2] << 32) | m[3];
+  mine = tied;
 }
 
 // Slot of a bucket held by `lane` in the coalesced score layout: q = 0, 1
@@ -485,7 +520,7 @@ __device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_
 constexpr int kPrefetchAhead = 1;  // victim searches whose lines are prefetched ahead
 
 template <bool VEC16>
-__global__ void __launch_bounds__(kInsThreads, 4)
+__global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
     insert_kernel(TableDev t, Scratch s, const float* __restrict__ values,
                   const uint64_t* __restrict__ scores_in, ScoreCtx ctx) {
   if (aborted(s)) return;
@@ -619,23 +654,15 @@ __global__ void __launch_bounds__(kInsThreads, 4)
           }
         }
         kreads += two ? 8 : 4;
-        unsigned long long smin = bs, kmin = bk;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-          const unsigned long long os = __shfl_xor_sync(kFull, smin, o);
-          const unsigned long long ok2 = __shfl_xor_sync(kFull, kmin, o);
-          if (sk_less(os, ok2, smin, kmin)) {
-            smin = os;
-            kmin = ok2;
-          }
-        }
-        lockmin = shfl_min_u64(lockmin);
+        unsigned long long smin, kmin;
+        bool mine;
+        warp_min_sk(bs, bk, smin, kmin, mine);
+        lockmin = warp_min_u64(lockmin);
         if (lockmin <= smin || kmin == ~0ull) {
           why = kmin == ~0ull ? 2u : 1u;
           retries += lane == 0;
           continue;
         }
-        const unsigned long long kbest = bk;
         const int qbest = bq;
         // Admission control: admit iff (s, k) > (s_min, k_min).
         if (!sk_less(smin, kmin, sc, key)) {
@@ -643,7 +670,7 @@ __global__ void __launch_bounds__(kInsThreads, 4)
           rejected++;
           break;
         }
-        const unsigned own = __ballot_sync(kFull, qbest >= 0 && kbest == kmin);
+        const unsigned own = __ballot_sync(kFull, qbest >= 0 && mine);
         const int owner = __ffs(own) - 1;
         int ok = 0, stale = 0;
         uint64_t g = 0;
@@ -922,7 +949,7 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
   launch_dedup(t, n, keys, s, st);
   launch_update<true>(t, n, s, values, scores, ctx, vec16, st);
   {
-    const unsigned ig = grid_for(t, (n + 31) / 32 * 32, kInsThreads, 4);
+    const unsigned ig = grid_for(t, (n + 31) / 32 * 32, kInsThreads, kInsBlocksPerSm);
     KernelTimer timer(t->prof, HKV_K_INSERT, st);
     if (vec16)
       insert_kernel<true><<<ig, kInsThreads, 0, st>>>(t->dev, s, values, scores, ctx);
@@ -1039,7 +1066,7 @@ hkv_status launch_upsert_in(hkv_table_s* t, uint64_t n, const uint64_t* keys, co
   launch_dedup(t, n, keys, s, st);
   launch_update<true>(t, n, s, values, scores, ctx, vec16, st);
   {
-    const unsigned ig = grid_for(t, (n + 31) / 32 * 32, kInsThreads, 4);
+    const unsigned ig = grid_for(t, (n + 31) / 32 * 32, kInsThreads, kInsBlocksPerSm);
     KernelTimer timer(t->prof, HKV_K_INSERT, st);
     if (vec16)
       insert_kernel<true><<<ig, kInsThreads, 0, st>>>(t->dev, s, values, scores, ctx);
@@ -1096,7 +1123,7 @@ hkv_status launch_upsert_desc(hkv_table_s* t, uint64_t n_max, const OpDesc* d, v
   clear_kernel<<<grid_for(t, s.tab_mask + 1, 256, 8), 256, 0, st>>>(s);
   launch_dedup(t, n, nullptr, s, st);
   launch_update<true>(t, n, s, nullptr, nullptr, ScoreCtx{0, 0}, vec16, st);
-  const unsigned ig = grid_for(t, (n + 31) / 32 * 32, kInsThreads, 4);
+  const unsigned ig = grid_for(t, (n + 31) / 32 * 32, kInsThreads, kInsBlocksPerSm);
   if (vec16)
     insert_kernel<true><<<ig, kInsThreads, 0, st>>>(t->dev, s, nullptr, nullptr, ScoreCtx{0, 0});
   else
