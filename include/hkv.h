@@ -329,6 +329,37 @@ hkv_status hkv_serve_run(hkv_server_t s, const hkv_serve_request *reqs, uint64_t
                          hkv_stream_t stream);
 hkv_status hkv_serve_destroy(hkv_server_t s);
 
+/* Host-buffer pipeline (the paper has no host API; this is the library's
+ * end-to-end path). A pipeline owns `depth` (2..8) staging slots in HBM,
+ * each big enough for max_keys keys with rows of up to max_dim floats, and
+ * three streams: copy-in, compute, copy-out. hkv_pipeline_find and
+ * hkv_pipeline_insert_or_assign take HOST buffers, queue the host-to-device
+ * copy of the inputs into the next slot, the table operation on the compute
+ * stream (hkv_find / hkv_insert_or_assign, with their results, statuses and
+ * table roles) and the device-to-host copy of the results, and return at
+ * once. So operation k's input copy overlaps operation k-1's kernels and
+ * operation k-2's result copy; a slot is reused only after its previous
+ * results reached the host. Operations run in call order, also across
+ * tables. Host buffers must stay valid and untouched until
+ * hkv_pipeline_sync returns; page-locked memory (cudaHostAlloc or
+ * cudaHostRegister) is needed for the copies to overlap, pageable memory
+ * works but serialises them. Arguments: keys [n], values [n][dim] (find:
+ * output, the rows of misses are zeros; upsert: input), found[n] /
+ * status[n] (nullable), scores[n] (HKV_CUSTOM upserts, else NULL).
+ * HKV_ERR_INVALID_ARG for n > max_keys, dim > max_dim or a null required
+ * buffer; evictions are not reported. */
+typedef struct hkv_pipeline_s *hkv_pipeline_t;
+hkv_status hkv_pipeline_create(uint64_t max_keys, uint32_t max_dim, int depth,
+                               hkv_pipeline_t *out);
+hkv_status hkv_pipeline_find(hkv_pipeline_t p, hkv_table_t t, uint64_t n, const uint64_t *keys,
+                             float *values, uint8_t *found);
+hkv_status hkv_pipeline_insert_or_assign(hkv_pipeline_t p, hkv_table_t t, uint64_t n,
+                                         const uint64_t *keys, const float *values,
+                                         const uint64_t *scores, uint8_t *status);
+/* Wait until every queued operation's results are in host memory. */
+hkv_status hkv_pipeline_sync(hkv_pipeline_t p);
+hkv_status hkv_pipeline_destroy(hkv_pipeline_t p);
+
 /* Measurement hook. While enabled, every kernel the library launches for
  * this table is bracketed by two CUDA events recorded on the launching
  * stream. hkv_profile_read waits for those events and returns, per kernel

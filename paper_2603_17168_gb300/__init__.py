@@ -85,6 +85,11 @@ SIGNATURES = {
     "hkv_serve_run": (_i32, [_vp, ctypes.POINTER(ServeRequest), _u64, _i32, _i32,
                              ctypes.POINTER(ServeResult), _vp]),
     "hkv_serve_destroy": (_i32, [_vp]),
+    "hkv_pipeline_create": (_i32, [_u64, _u32, _i32, ctypes.POINTER(_vp)]),
+    "hkv_pipeline_find": (_i32, [_vp, _vp, _u64, _vp, _vp, _vp]),
+    "hkv_pipeline_insert_or_assign": (_i32, [_vp, _vp, _u64, _vp, _vp, _vp, _vp]),
+    "hkv_pipeline_sync": (_i32, [_vp]),
+    "hkv_pipeline_destroy": (_i32, [_vp]),
     "hkv_profile_enable": (_i32, [_vp, _i32]),
     "hkv_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), _P64]),
     "hkv_last_error": (ctypes.c_char_p, []),
@@ -398,6 +403,43 @@ class Batch:
             sc = o.get("scores")
             arr[i].scores = sc.data_ptr() if sc is not None else None
         _check(load_library().hkv_batch_run(self._h, arr, int(use_graph), _stream(stream)))
+
+
+class Pipeline:
+    """Host-buffer pipeline (see hkv_pipeline_* in include/hkv.h): find and
+    insert_or_assign on HOST tensors (page-locked for overlap), queued with
+    their copies so that neighbouring operations' copies and kernels
+    overlap. Results are in the host tensors after sync()."""
+
+    def __init__(self, max_keys, max_dim, depth=3):
+        h = ctypes.c_void_p()
+        _check(load_library().hkv_pipeline_create(int(max_keys), int(max_dim), int(depth),
+                                                   ctypes.byref(h)))
+        self._h = h
+
+    def find(self, table, keys, values, found=None, n=None):
+        n = keys.numel() if n is None else int(n)
+        _check(load_library().hkv_pipeline_find(self._h, table.handle, n, _ptr(keys),
+                                                 _ptr(values), _ptr(found)))
+
+    def insert_or_assign(self, table, keys, values, scores=None, status=None, n=None):
+        n = keys.numel() if n is None else int(n)
+        _check(load_library().hkv_pipeline_insert_or_assign(
+            self._h, table.handle, n, _ptr(keys), _ptr(values), _ptr(scores), _ptr(status)))
+
+    def sync(self):
+        _check(load_library().hkv_pipeline_sync(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(load_library().hkv_pipeline_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -55,3 +55,16 @@ def test_invalid_arguments_fail_without_touching_the_gpu(lib):
     lib.hkv_create.restype = ctypes.c_int
     lib.hkv_create.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     assert lib.hkv_create(None, None) == 1
+
+
+def test_pipeline_refuses_bad_arguments_without_gpu(lib):
+    lib.hkv_pipeline_create.restype = ctypes.c_int
+    lib.hkv_pipeline_create.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                        ctypes.c_void_p]
+    h = ctypes.c_void_p()
+    assert lib.hkv_pipeline_create(0, 8, 3, ctypes.byref(h)) == 1      # no keys
+    assert lib.hkv_pipeline_create(100, 8, 1, ctypes.byref(h)) == 1    # depth below 2
+    assert lib.hkv_pipeline_create(100, 8, 9, ctypes.byref(h)) == 1    # depth above 8
+    lib.hkv_pipeline_sync.restype = ctypes.c_int
+    lib.hkv_pipeline_sync.argtypes = [ctypes.c_void_p]
+    assert lib.hkv_pipeline_sync(None) == 1
