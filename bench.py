@@ -56,6 +56,8 @@ def parse_args(argv=None):
     p.add_argument("--batch", type=int, default=BATCH)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-random-access", action="store_true",
+                   help="skip the random-access ceiling measurement")
     p.add_argument("--find-tpk", type=int, default=0)
     p.add_argument("--update-tpk", type=int, default=0)
     p.add_argument("--workload", choices=("single", "multi", "serve", "tiered"), default="single")
@@ -248,6 +250,45 @@ def kernel_bytes(kind: str, c: dict, n_calls: int, batch: int, dim: int) -> floa
     return 0.0
 
 
+RANDOM_KINDS = ("line_reads", "sector_reads", "line_writes", "sector_writes")
+
+
+def kernel_random_accesses(kind: str, c: dict, n_calls: int, batch: int, dim: int):
+    """Scattered DRAM accesses of a probe kernel from the device counters,
+    {line_reads, sector_reads, line_writes, sector_writes} (128-B lines,
+    32-B sectors), plus the bytes it streams in order (batch keys, flags,
+    output rows written by batch index). L2-resident scratch (the dedup
+    table, the occupancy counters) is not counted."""
+    D = 4 * dim
+    uc = c.get("upd_claims", 0)
+    if kind == "find":
+        return {"line_reads": c["find_lines"] + c["find_hit"], "sector_reads": c["find_keys"],
+                "line_writes": 0, "sector_writes": 0,
+                "stream_bytes": n_calls * batch * 9 + D * c["find_hit"]}
+    if kind == "update":
+        u = c["unique"]
+        # probe lines and key confirms; an update reads its input row and
+        # its score sector and writes the value row and the score; a claim
+        # reads its input row and the key sector (CAS) and writes the value
+        # row and the key, score and digest sectors
+        return {"line_reads": c["upd_lines"] + c["updated"] + uc,
+                "sector_reads": c["upd_keys"] + c["updated"] + uc,
+                "line_writes": c["updated"] + uc,
+                "sector_writes": c["updated"] + 3 * uc,
+                "stream_bytes": u * 13 + (u - c["updated"] - uc) * 8}
+    return None
+
+
+def measure_random_ceiling():
+    """Random-access rates of this GPU's HBM (accesses/s) over an 8 GiB
+    buffer: 128-B line and 32-B sector reads and writes."""
+    import paper_2603_17168_gb300 as hkv
+    return {"line_reads": hkv.measure_random_access(128),
+            "sector_reads": hkv.measure_random_access(32),
+            "line_writes": hkv.measure_random_access(128, write=True),
+            "sector_writes": hkv.measure_random_access(32, write=True)}
+
+
 # -------------------------------------------------------------------- ours
 
 def fill_table(t, lam, gen, dim, batch_fill=1 << 20, max_batches=400):
@@ -289,6 +330,7 @@ def run_ours(args):
 
     nvtx = torch.cuda.nvtx
     lambdas = args.lambdas
+    ceiling = None if args.no_random_access else measure_random_ceiling()
     tables, lam_fill = [], []
     nvtx.range_push("fill")
     for lam in lambdas:
@@ -380,10 +422,20 @@ def run_ours(args):
         c = per_lambda[li]["_counters"]
         per_lambda[li]["kernel_ms"] = {k: round(v[0], 4) for k, v in prof.items()}
         for kind, (kms, launches) in prof.items():
-            e = kinds.setdefault(kind, {"ms": 0.0, "launches": 0, "bytes": 0.0})
+            e = kinds.setdefault(kind, {"ms": 0.0, "launches": 0, "bytes": 0.0, "ra": None})
             e["ms"] += kms
             e["launches"] += launches
             e["bytes"] += kernel_bytes(kind, c, steps, batch, DIM)
+            ra = kernel_random_accesses(kind, c, steps, batch, DIM)
+            if ra is not None:
+                acc = e["ra"] or dict.fromkeys(ra, 0)
+                e["ra"] = {k: acc[k] + ra[k] for k in ra}
+    for kind, e in kinds.items():
+        e["ra_frac"] = None
+        if ceiling and e["ra"] and e["ms"] > 0:
+            e["ra_bound_ms"] = 1e3 * (sum(e["ra"][k] / ceiling[k] for k in RANDOM_KINDS)
+                                      + e["ra"]["stream_bytes"] / (peak * 1e9))
+            e["ra_frac"] = e["ra_bound_ms"] / e["ms"]
     for kind, e in kinds.items():
         e["gbs"] = e["bytes"] / (e["ms"] * 1e6) if e["ms"] > 0 else None
         e["frac_measured"] = e["gbs"] / peak if e["gbs"] else None
@@ -399,6 +451,19 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": round(d["bytes"] / d["launches"]),
                 "avg_launch_ms": round(d["ms"] / d["launches"], 5),
                 "traffic": traffic}
+    if d.get("ra_frac") is not None:
+        n_l = d["launches"]
+        roofline["random_access"] = {
+            "note": "the same kernel against the random-access rate of this GPU's HBM, "
+                    "measured in this run (hkv_measure_random_access, 8 GiB buffer): each "
+                    "scattered 128-B line or 32-B sector access per launch (device counters) "
+                    "costed at the measured rate of its kind, plus the bytes streamed in order "
+                    "at the copy peak; frac = that bound / the measured launch time",
+            "ceiling": {k: round(v / 1e9, 2) for k, v in ceiling.items()},
+            "ceiling_unit": "G accesses/s",
+            "per_launch": {k: round(v / n_l) for k, v in d["ra"].items()},
+            "bound_ms_per_launch": round(d["ra_bound_ms"] / n_l, 5),
+            "frac": round(d["ra_frac"], 4)}
     gpu_launches = sum(e["launches"] for e in kinds.values())
     for e in per_lambda:
         e.pop("_counters")
@@ -430,7 +495,8 @@ def run_ours(args):
             "kernels": {k: {"ms": round(v["ms"], 4), "launches": v["launches"],
                             "share": round(v["share"], 4),
                             "gbs": round(v["gbs"], 1) if v["gbs"] else None,
-                            "frac_measured": round(v["frac_measured"], 4) if v["frac_measured"] else None}
+                            "frac_measured": round(v["frac_measured"], 4) if v["frac_measured"] else None,
+                            "frac_random_access": round(v["ra_frac"], 4) if v["ra_frac"] else None}
                         for k, v in sorted(kinds.items(), key=lambda kv: -kv[1]["ms"])},
             "roofline": roofline, "gpu_launches": gpu_launches, "clocks": clk, "e2e": e2e,
         }

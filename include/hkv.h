@@ -381,6 +381,22 @@ enum {
 hkv_status hkv_profile_enable(hkv_table_t t, int on);
 hkv_status hkv_profile_read(hkv_table_t t, double *ms_out, uint64_t *launches_out);
 
+/* Random-access rate of device memory (a measurement hook; the paper has
+ * none). Hash-table kernels touch scattered lines and sectors, whose rate
+ * HBM bounds well below its sequential copy bandwidth; this is the ceiling
+ * their roofline is read against. Touches `accesses` uniformly random,
+ * naturally aligned units of unit_bytes (8, 32 or 128) in a scratch buffer
+ * of buffer_bytes (a multiple of 128, at least 1 MiB; allocated and freed
+ * here, and far above L2 for a meaningful number; the units used span the
+ * largest power of two of them that fits), reading (write = 0) or
+ * writing (write = 1) each, with 8 independent accesses in flight per
+ * thread, and stores the best of `repeats` timed launches in
+ * *accesses_per_s (host). Synchronous, on the current device.
+ * HKV_ERR_INVALID_ARG for other arguments, HKV_ERR_OOM if the buffer cannot
+ * be allocated. */
+hkv_status hkv_measure_random_access(uint32_t unit_bytes, int write, uint64_t buffer_bytes,
+                                     uint64_t accesses, int repeats, double *accesses_per_s);
+
 /* Message of the calling thread's last error ("" if none). */
 const char *hkv_last_error(void);
 

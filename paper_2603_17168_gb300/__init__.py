@@ -92,6 +92,8 @@ SIGNATURES = {
     "hkv_pipeline_destroy": (_i32, [_vp]),
     "hkv_profile_enable": (_i32, [_vp, _i32]),
     "hkv_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), _P64]),
+    "hkv_measure_random_access": (_i32, [_u32, _i32, _u64, _u64, _i32,
+                                          ctypes.POINTER(ctypes.c_double)]),
     "hkv_last_error": (ctypes.c_char_p, []),
 }
 
@@ -403,6 +405,17 @@ class Batch:
             sc = o.get("scores")
             arr[i].scores = sc.data_ptr() if sc is not None else None
         _check(load_library().hkv_batch_run(self._h, arr, int(use_graph), _stream(stream)))
+
+
+def measure_random_access(unit_bytes, write=False, buffer_bytes=8 << 30, accesses=64 << 20,
+                          repeats=3):
+    """Random accesses per second of `unit_bytes` units (8, 32 or 128) over a
+    buffer far above L2 (see hkv_measure_random_access)."""
+    out = ctypes.c_double()
+    _check(load_library().hkv_measure_random_access(int(unit_bytes), int(bool(write)),
+                                                     int(buffer_bytes), int(accesses),
+                                                     int(repeats), ctypes.byref(out)))
+    return out.value
 
 
 class Pipeline:

@@ -132,10 +132,12 @@ hkv_status hkv_pipeline_find(hkv_pipeline_t p, hkv_table_t t, uint64_t n, const 
   const uint64_t row_bytes = n * t->opts.dim * 4ull;
   PipeSlot& s = take_slot(p);
   cudaMemcpyAsync(s.keys, keys, n * 8, cudaMemcpyHostToDevice, p->in);
-  // rows of misses come back as zeros (cleared on the device, not sent)
-  cudaMemsetAsync(s.rows, 0, row_bytes, p->in);
   cudaEventRecord(s.in_done, p->in);
   cudaStreamWaitEvent(p->compute, s.in_done, 0);
+  // Rows of misses come back as zeros: cleared on the device (on the compute
+  // stream, which has slack, not on the copy-in stream, which is the link's
+  // critical path), not sent.
+  cudaMemsetAsync(s.rows, 0, row_bytes, p->compute);
   hkv_status rc = hkv_find(t, n, s.keys, s.rows, s.flags, nullptr, p->compute);
   cudaEventRecord(s.compute_done, p->compute);
   cudaStreamWaitEvent(p->out, s.compute_done, 0);

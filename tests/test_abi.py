@@ -68,3 +68,15 @@ def test_pipeline_refuses_bad_arguments_without_gpu(lib):
     lib.hkv_pipeline_sync.restype = ctypes.c_int
     lib.hkv_pipeline_sync.argtypes = [ctypes.c_void_p]
     assert lib.hkv_pipeline_sync(None) == 1
+
+
+def test_random_access_measurement_refuses_bad_arguments_without_gpu(lib):
+    f = lib.hkv_measure_random_access
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_uint32, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                  ctypes.c_void_p]
+    out = ctypes.c_double()
+    assert f(16, 0, 1 << 30, 1 << 20, 1, ctypes.byref(out)) == 1       # unit not 8/32/128
+    assert f(128, 0, (1 << 30) + 8, 1 << 20, 1, ctypes.byref(out)) == 1  # not a multiple of 128
+    assert f(128, 0, 1 << 30, 0, 1, ctypes.byref(out)) == 1            # no accesses
+    assert f(128, 0, 1 << 30, 1 << 20, 1, None) == 1                   # no output
