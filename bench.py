@@ -56,6 +56,8 @@ def parse_args(argv=None):
     p.add_argument("--batch", type=int, default=BATCH)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--l2-residency", action="store_true",
+                   help="keep each table's digest array persisting in L2 (hkv_set_l2_residency)")
     p.add_argument("--no-random-access", action="store_true",
                    help="skip the random-access ceiling measurement")
     p.add_argument("--find-tpk", type=int, default=0)
@@ -336,6 +338,8 @@ def run_ours(args):
     for lam in lambdas:
         t = hkv.Table(nb * 128, DIM, hkv.LFU, dual_bucket=True)
         t.set_launch(args.find_tpk, args.update_tpk)
+        if args.l2_residency:
+            t.set_l2_residency(nb * 128)
         lam_fill.append(fill_table(t, lam, gen, DIM))
         tables.append(t)
     nvtx.range_pop()
@@ -490,7 +494,8 @@ def run_ours(args):
                        "l2": "no flush: each table is 9.1 GiB and a step's inputs 1.1 GiB, "
                              "both far above the 129 MB L2",
                        "launch": {"find_tpk": args.find_tpk or "default",
-                                  "update_tpk": args.update_tpk or "default"}},
+                                  "update_tpk": args.update_tpk or "default"},
+                       "l2_residency_bytes": [t.l2_residency for t in tables]},
             "per_lambda": per_lambda,
             "kernels": {k: {"ms": round(v["ms"], 4), "launches": v["launches"],
                             "share": round(v["share"], 4),

@@ -252,6 +252,20 @@ hkv_status hkv_reset_counters(hkv_table_t t, hkv_stream_t stream);
  * these; defaults follow the value width. */
 hkv_status hkv_set_launch(hkv_table_t t, int find_threads_per_key, int update_threads_per_key);
 
+/* L2 residency of the digest array (no counterpart in the paper; the
+ * GB300's 126 MB L2 holds the whole digest array of a table up to 2^26
+ * slots). Every probe reads a bucket's 128-byte digest line before anything
+ * else; with a residency set, the probe and fill kernels of this table
+ * launch with an access-policy window that marks its first digest_bytes of
+ * digest lines persisting in L2 (0: no window). The window is capped at the device's
+ * window limit, and the context's persisting L2 set-aside is raised to the
+ * device maximum (a per-context limit, released with the context). Tables
+ * start without a window. hkv_l2_residency
+ * returns the bytes the window covers (0 if none, or if the device has no
+ * persisting L2). */
+hkv_status hkv_set_l2_residency(hkv_table_t t, uint64_t digest_bytes);
+uint64_t hkv_l2_residency(hkv_table_t t);
+
 /* Batched multi-table rounds (the paper has no batched multi-table API;
  * this is the library's serving-side addition). A batch object binds
  * n_slots distinct tables, each with the largest number of keys a round

@@ -77,6 +77,8 @@ SIGNATURES = {
     "hkv_read_counters": (_i32, [_vp, _P64, _vp]),
     "hkv_reset_counters": (_i32, [_vp, _vp]),
     "hkv_set_launch": (_i32, [_vp, _i32, _i32]),
+    "hkv_set_l2_residency": (_i32, [_vp, _u64]),
+    "hkv_l2_residency": (_u64, [_vp]),
     "hkv_batch_create": (_i32, [_i32, ctypes.POINTER(_vp), _P64, ctypes.POINTER(_vp)]),
     "hkv_batch_run": (_i32, [_vp, ctypes.POINTER(BatchOp), _i32, _vp]),
     "hkv_batch_destroy": (_i32, [_vp]),
@@ -325,6 +327,14 @@ class Table:
     def set_launch(self, find_threads_per_key: int = 0, update_threads_per_key: int = 0):
         _check(load_library().hkv_set_launch(self._h, find_threads_per_key,
                                              update_threads_per_key))
+
+    def set_l2_residency(self, digest_bytes: int):
+        """Bytes of the digest array kept persisting in L2 (0: off)."""
+        _check(load_library().hkv_set_l2_residency(self._h, int(digest_bytes)))
+
+    @property
+    def l2_residency(self) -> int:
+        return int(load_library().hkv_l2_residency(self._h))
 
 
 class Batch:

@@ -87,14 +87,14 @@ void launch_g(const hkv_table_s* t, uint64_t n, const uint64_t* keys, float* out
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   if (!values)
-    find_kernel<G, false, false><<<(unsigned)blocks, kFindThreads, 0, s>>>(t->dev, n, keys, out,
-                                                                           found, scores_out, d);
+    launch_table_kernel(t, find_kernel<G, false, false>, (unsigned)blocks, kFindThreads, 0, s,
+                        t->dev, n, keys, out, found, scores_out, d);
   else if (vec16)
-    find_kernel<G, true, true><<<(unsigned)blocks, kFindThreads, 0, s>>>(t->dev, n, keys, out,
-                                                                         found, scores_out, d);
+    launch_table_kernel(t, find_kernel<G, true, true>, (unsigned)blocks, kFindThreads, 0, s,
+                        t->dev, n, keys, out, found, scores_out, d);
   else
-    find_kernel<G, false, true><<<(unsigned)blocks, kFindThreads, 0, s>>>(t->dev, n, keys, out,
-                                                                          found, scores_out, d);
+    launch_table_kernel(t, find_kernel<G, false, true>, (unsigned)blocks, kFindThreads, 0, s,
+                        t->dev, n, keys, out, found, scores_out, d);
 }
 
 }  // namespace

@@ -118,7 +118,40 @@ struct hkv_table_s {
   cudaMemPool_t pool = nullptr;         // stream-ordered scratch allocations
   hkv::TripleGroup<hkv::CudaEvents> sched;
   hkv::Profiler prof;
+  // L2 residency of the digest array: the access-policy window its probe
+  // kernels launch with (num_bytes 0: none).
+  cudaAccessPolicyWindow l2win{};
 };
+
+namespace hkv {
+
+// Launch a kernel that probes or fills t's buckets with the table's L2
+// window on its digest array as a per-launch attribute, so the caller's
+// stream keeps its own attributes.
+template <typename... KArgs, typename... Args>
+inline void launch_table_kernel(const hkv_table_s* t, void (*kernel)(KArgs...), unsigned grid,
+                                unsigned block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr{};
+  if (t->l2win.num_bytes) {
+    attr.id = cudaLaunchAttributeAccessPolicyWindow;
+    attr.val.accessPolicyWindow = t->l2win;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+  }
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// Window covering the first `want` bytes of t's digest array (0: none),
+// sized to the device's window limit and to the persisting L2 set-aside,
+// which it raises as far as the device allows (a per-context limit).
+void set_l2_window(hkv_table_s* t, uint64_t want);
+
+}  // namespace hkv
 
 namespace hkv {
 

@@ -97,6 +97,33 @@ hkv_status cuda_status(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? HKV_ERR_OOM : HKV_ERR_CUDA;
 }
 
+void set_l2_window(hkv_table_s* t, uint64_t want) {
+  t->l2win = cudaAccessPolicyWindow{};
+  const uint64_t digest_bytes = t->num_buckets * kSlots;
+  if (want > digest_bytes) want = digest_bytes;
+  if (want == 0) return;
+  int max_win = 0, max_persist = 0;
+  cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, t->device);
+  cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, t->device);
+  if (max_win <= 0 || max_persist <= 0) return;  // no persisting L2 on this device
+  size_t cur = 0;
+  cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+  if (cur < (size_t)max_persist &&
+      cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)max_persist) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+  const uint64_t bytes = std::min<uint64_t>(want, (uint64_t)max_win);
+  t->l2win.base_ptr = t->dev.digests;
+  t->l2win.num_bytes = bytes;
+  // more window than set-aside: mark only that share persisting, so the
+  // persisting lines do not evict each other
+  t->l2win.hitRatio = std::min(1.0f, (float)((double)cur / (double)bytes));
+  t->l2win.hitProp = cudaAccessPropertyPersisting;
+  t->l2win.missProp = cudaAccessPropertyStreaming;
+}
+
 hkv_status launch_size(hkv_table_s* t, unsigned long long* out_dev, cudaStream_t s) {
   cudaMemsetAsync(out_dev, 0, 8, s);
   const uint64_t n16 = t->num_buckets * kSlots / 16;
@@ -275,6 +302,9 @@ hkv_status hkv_create(const hkv_options* o, hkv_table_t* out) {
   // more lanes for the row copy.
   t->launch.find_tpk = t->opts.dim <= 32 ? 2 : (t->opts.dim <= 128 ? 4 : 8);
   t->launch.update_tpk = t->opts.dim <= 128 ? 2 : 4;
+  // No L2 window by default: on the four-table workload a window over each
+  // table's digest array made every probe kernel slower (hkv_set_l2_residency
+  // turns it on per table).
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     free_table(t);
@@ -283,6 +313,18 @@ hkv_status hkv_create(const hkv_options* o, hkv_table_t* out) {
   *out = t;
   return HKV_OK;
 }
+
+hkv_status hkv_set_l2_residency(hkv_table_t t, uint64_t digest_bytes) {
+  if (bad(t)) return fail(HKV_ERR_INVALID_ARG, "null table");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaSetDevice(t->device);
+  set_l2_window(t, digest_bytes);
+  cudaSetDevice(dev);
+  return HKV_OK;
+}
+
+uint64_t hkv_l2_residency(hkv_table_t t) { return bad(t) ? 0 : t->l2win.num_bytes; }
 
 hkv_status hkv_destroy(hkv_table_t t) {
   if (bad(t)) return fail(HKV_ERR_INVALID_ARG, "null table");

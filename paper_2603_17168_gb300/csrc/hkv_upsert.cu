@@ -901,9 +901,11 @@ void launch_update_g(hkv_table_s* t, uint64_t n, const Scratch& s, const float* 
   const unsigned grid = grid_for(t, n * G, kUpdThreads, 2 * kUpdBlocksPerSm);
   KernelTimer timer(t->prof, HKV_K_UPDATE, st);
   if (vec16)
-    update_kernel<G, true, UPSERT><<<grid, kUpdThreads, 0, st>>>(t->dev, s, values, scores, ctx);
+    launch_table_kernel(t, update_kernel<G, true, UPSERT>, grid, kUpdThreads, 0, st, t->dev, s,
+                        values, scores, ctx);
   else
-    update_kernel<G, false, UPSERT><<<grid, kUpdThreads, 0, st>>>(t->dev, s, values, scores, ctx);
+    launch_table_kernel(t, update_kernel<G, false, UPSERT>, grid, kUpdThreads, 0, st, t->dev, s,
+                        values, scores, ctx);
 }
 
 template <bool UPSERT>
@@ -952,9 +954,11 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
     const unsigned ig = grid_for(t, (n + 31) / 32 * 32, kInsThreads, kInsBlocksPerSm);
     KernelTimer timer(t->prof, HKV_K_INSERT, st);
     if (vec16)
-      insert_kernel<true><<<ig, kInsThreads, 0, st>>>(t->dev, s, values, scores, ctx);
+      launch_table_kernel(t, insert_kernel<true>, ig, kInsThreads, 0, st, t->dev, s, values,
+                          scores, ctx);
     else
-      insert_kernel<false><<<ig, kInsThreads, 0, st>>>(t->dev, s, values, scores, ctx);
+      launch_table_kernel(t, insert_kernel<false>, ig, kInsThreads, 0, st, t->dev, s, values,
+                          scores, ctx);
   }
   {
     KernelTimer timer(t->prof, HKV_K_RECONCILE, st);
@@ -1069,9 +1073,11 @@ hkv_status launch_upsert_in(hkv_table_s* t, uint64_t n, const uint64_t* keys, co
     const unsigned ig = grid_for(t, (n + 31) / 32 * 32, kInsThreads, kInsBlocksPerSm);
     KernelTimer timer(t->prof, HKV_K_INSERT, st);
     if (vec16)
-      insert_kernel<true><<<ig, kInsThreads, 0, st>>>(t->dev, s, values, scores, ctx);
+      launch_table_kernel(t, insert_kernel<true>, ig, kInsThreads, 0, st, t->dev, s, values,
+                          scores, ctx);
     else
-      insert_kernel<false><<<ig, kInsThreads, 0, st>>>(t->dev, s, values, scores, ctx);
+      launch_table_kernel(t, insert_kernel<false>, ig, kInsThreads, 0, st, t->dev, s, values,
+                          scores, ctx);
   }
   {
     KernelTimer timer(t->prof, HKV_K_RECONCILE, st);
@@ -1125,9 +1131,11 @@ hkv_status launch_upsert_desc(hkv_table_s* t, uint64_t n_max, const OpDesc* d, v
   launch_update<true>(t, n, s, nullptr, nullptr, ScoreCtx{0, 0}, vec16, st);
   const unsigned ig = grid_for(t, (n + 31) / 32 * 32, kInsThreads, kInsBlocksPerSm);
   if (vec16)
-    insert_kernel<true><<<ig, kInsThreads, 0, st>>>(t->dev, s, nullptr, nullptr, ScoreCtx{0, 0});
+    launch_table_kernel(t, insert_kernel<true>, ig, kInsThreads, 0, st, t->dev, s,
+                        (const float*)nullptr, (const uint64_t*)nullptr, ScoreCtx{0, 0});
   else
-    insert_kernel<false><<<ig, kInsThreads, 0, st>>>(t->dev, s, nullptr, nullptr, ScoreCtx{0, 0});
+    launch_table_kernel(t, insert_kernel<false>, ig, kInsThreads, 0, st, t->dev, s,
+                        (const float*)nullptr, (const uint64_t*)nullptr, ScoreCtx{0, 0});
   reconcile_kernel<<<grid_for(t, n, kRecThreads, 8), kRecThreads, 0, st>>>(t->dev, s, nullptr,
                                                                              nullptr, nullptr);
   status_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(n, s, nullptr, nullptr);
