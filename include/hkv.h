@@ -89,7 +89,13 @@ typedef struct {
   int32_t policy;          /* hkv_policy */
   int32_t dual_bucket;     /* 1: two candidate buckets per key (Sec. 3.4) */
   int32_t deterministic;   /* 1: a batch holding a key twice is refused with
-                              HKV_ERR_DUPLICATE_KEY */
+                              HKV_ERR_DUPLICATE_KEY. With dual_bucket, phase
+                              I then runs key by key in batch order (in
+                              waves of keys with disjoint buckets), so the
+                              table equals sequential Algorithm 3 bit for
+                              bit; hkv_insert_or_assign returns once phase
+                              I is done, and the no-alloc, batch and serve
+                              paths refuse such tables */
   uint64_t hbm_value_budget_bytes; /* value bytes kept in HBM; the rest go to
                                       pinned mapped host memory. 0 = all HBM */
   uint64_t slice_bytes;    /* value slice size (Sec. 4.2); 0 = 1 GiB. Rounded

@@ -95,6 +95,9 @@ hkv_status hkv_batch_create(int n_slots, const hkv_table_t* tables, const uint64
       return bad_arg("each slot needs a table and 0 < max_keys < 2^31");
     for (int j = 0; j < i; ++j)
       if (tables[j] == tables[i]) return bad_arg("a table may appear in one slot only");
+    // their ordered phase I is driven from the host, which a graph cannot do
+    if (tables[i]->opts.deterministic && tables[i]->dev.dual)
+      return bad_arg("deterministic dual-bucket tables take hkv_insert_or_assign only");
   }
   hkv_batch_s* b = new hkv_batch_s();
   cudaGetDevice(&b->device);

@@ -121,6 +121,7 @@ struct hkv_table_s {
   // L2 residency of the digest array: the access-policy window its probe
   // kernels launch with (num_bytes 0: none).
   cudaAccessPolicyWindow l2win{};
+  unsigned long long* host_word = nullptr;  // pinned word for device-to-host counts
 };
 
 namespace hkv {

@@ -158,6 +158,7 @@ void free_table(hkv_table_s* t) {
   if (t->slices_dev) cudaFree(t->slices_dev);
   if (t->meta) cudaFree(t->meta);
   if (t->pool) cudaMemPoolDestroy(t->pool);
+  if (t->host_word) cudaFreeHost(t->host_word);
   delete t;
 }
 
@@ -292,6 +293,12 @@ hkv_status hkv_create(const hkv_options* o, hkv_table_t* out) {
     return cuda_status(e, "scratch pool");
   }
 
+  e = cudaHostAlloc(reinterpret_cast<void**>(&t->host_word), 64, cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    t->host_word = nullptr;
+    free_table(t);
+    return cuda_status(e, "pinned word");
+  }
   init_meta_kernel<<<std::max(1, t->num_sms * 8), 256>>>(t->dev.digests, t->dev.keys,
                                                          t->dev.scores, slots);
   cudaMemset(t->dev.sizes, 0, nb * 4);

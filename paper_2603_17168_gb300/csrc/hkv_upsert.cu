@@ -48,7 +48,7 @@ struct DedupEntry {
 };
 static_assert(sizeof(DedupEntry) == 16, "dedup entry layout");
 
-enum : int { kCntUnique = 0, kCntEvOut = 1, kAbort = 2, kCntWords = 8 };
+enum : int { kCntUnique = 0, kCntEvOut = 1, kAbort = 2, kCntPending = 3, kCntWords = 8 };
 
 struct Scratch {
   DedupEntry* tab;
@@ -66,6 +66,8 @@ struct Scratch {
   uint64_t* evs;             // [n] its score
   float* evv;                // [n][dim] its value, or null
   const OpDesc* d;           // batched rounds: size, buffers and score context
+  unsigned long long* owner; // [B] ordered phase I: (wave, ~batch index) of
+                             // each bucket's first pending key, or null
 };
 
 __device__ __forceinline__ uint64_t dedup_pos(uint64_t key, int bits) {
@@ -428,13 +430,16 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
         }
       }
       if (UPSERT && lane_g == 0) {
-        // mflag: 0 placed (updated, or claimed here), 2 miss whose
-        // candidate buckets are all full. A miss claims its free slot right
+        // mflag: 0 placed (updated, or claimed here), 1 miss left to the
+        // ordered phase I, 2 miss whose candidate buckets are all full. A
+        // miss claims its free slot right
         // here: a claim into an empty slot cannot race the in-place updates
         // of this phase (they touch other slots); only evictions must wait
         // for phase U to end.
         uint8_t flag = 0;
-        if (!hit) {
+        if (!hit && s.owner) {
+          flag = 1;  // ordered phase I places it (deterministic dual-bucket mode)
+        } else if (!hit) {
           const uint64_t sc = policy_score(t.policy, false, 0, m, scores_in != nullptr,
                                            scores_in ? __ldg(scores_in + i) : 0, ctx);
           flag = claim_free_slot<VEC16>(t, s, e, key, h, sc, values + i * t.dim, ins_lines,
@@ -723,6 +728,136 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
   flush_counts(t, which, vals);
 }
 
+// ------------------------------------------------- ordered phase I (waves)
+//
+// Deterministic dual-bucket mode: phase I must equal Algorithm 3 run key by
+// key in batch order, because a key's D1 choice and D2 victim depend on what
+// earlier keys did to its two buckets. Keys run in waves: in wave w every
+// pending key bids for both candidate buckets with tag (w, ~i) (a 64-bit
+// atomicMax, so a bucket's word needs no reset between waves and holds the
+// smallest pending batch index i of the wave); a key that wins both of its
+// buckets runs Algorithm 3 alone on them. Keys of one wave touch disjoint
+// buckets, and every key runs after all earlier keys sharing a bucket with
+// it, so the result is the sequential one. The key with the smallest
+// pending i always wins, so the waves end after at most one per key.
+
+constexpr int kOrdThreads = 256;
+
+__device__ __forceinline__ unsigned long long wave_tag(uint64_t wave, uint32_t i) {
+  return (wave << 32) | (unsigned long long)(0xFFFFFFFFu - i);
+}
+
+__global__ void __launch_bounds__(kOrdThreads)
+    ordered_bid_kernel(TableDev t, Scratch s, uint64_t wave) {
+  if (aborted(s)) return;
+  const uint64_t nu = s.cnt[kCntUnique];
+  for (uint64_t u = blockIdx.x * (uint64_t)kOrdThreads + threadIdx.x; u < nu;
+       u += (uint64_t)gridDim.x * kOrdThreads) {
+    if (s.mflag[u] != 1) continue;
+    const uint64_t key = s.mkey[u];
+    const uint64_t b1 = fmix64(key) & t.bucket_mask;
+    const uint64_t b2 = t.dual ? second_bucket(t, key) : b1;
+    const unsigned long long tag = wave_tag(wave, s.mi[u]);
+    atomicMax(s.owner + b1, tag);
+    if (b2 != b1) atomicMax(s.owner + b2, tag);
+  }
+}
+
+// Minimum (score, key) of a full bucket, read by one thread.
+__device__ __forceinline__ int bucket_min(const TableDev& t, uint64_t b, uint64_t& smin,
+                                          uint64_t& kmin) {
+  int m = -1;
+  smin = ~0ull;
+  kmin = ~0ull;
+  for (int j = 0; j < (int)kSlots; ++j) {
+    const uint64_t x = b * kSlots + (uint64_t)j;
+    const uint64_t sj = __ldcg(reinterpret_cast<const unsigned long long*>(t.scores) + x);
+    const uint64_t kj = __ldcg(reinterpret_cast<const unsigned long long*>(t.keys) + x);
+    if (m < 0 || sk_less(sj, kj, smin, kmin)) {
+      m = j;
+      smin = sj;
+      kmin = kj;
+    }
+  }
+  return m;
+}
+
+template <bool VEC16>
+__global__ void __launch_bounds__(kOrdThreads)
+    ordered_insert_kernel(TableDev t, Scratch s, const float* __restrict__ values,
+                          const uint64_t* __restrict__ scores_in, ScoreCtx ctx, uint64_t wave) {
+  if (aborted(s)) return;
+  const uint64_t nu = s.cnt[kCntUnique];
+  unsigned pending = 0, inserted = 0, evicted = 0, rejected = 0;
+  for (uint64_t u = blockIdx.x * (uint64_t)kOrdThreads + threadIdx.x; u < nu;
+       u += (uint64_t)gridDim.x * kOrdThreads) {
+    if (s.mflag[u] != 1) continue;
+    const uint64_t key = s.mkey[u];
+    const uint32_t i = s.mi[u], m = s.mm[u], e = s.ulist[u];
+    const uint64_t h = fmix64(key);
+    const uint64_t b1 = h & t.bucket_mask;
+    const uint64_t b2 = t.dual ? second_bucket(t, key) : b1;
+    const bool two = b2 != b1;
+    const unsigned long long tag = wave_tag(wave, i);
+    if (__ldcg(s.owner + b1) != tag || (two && __ldcg(s.owner + b2) != tag)) {
+      pending++;
+      continue;
+    }
+    const uint64_t sc = policy_score(t.policy, false, 0, m, scores_in != nullptr,
+                                     scores_in ? __ldg(scores_in + i) : 0, ctx);
+    const float* src = values + (uint64_t)i * t.dim;
+    const uint32_t n1 = __ldcg(t.sizes + b1);
+    const uint32_t n2 = two ? __ldcg(t.sizes + b2) : kSlots;
+    uint64_t g = ~0ull, victim = kEmptyKey, vscore = 0;
+    if (n1 < kSlots || n2 < kSlots) {
+      // D1: the less occupied candidate, b1 on equal occupancy
+      const uint64_t b = n1 <= n2 ? b1 : b2;
+      unsigned sectors = 0;
+      const int slot = find_free(t.digests + b * kSlots, 0u, sectors);
+      if (slot < 0) {  // a counter out of step with its digests: refuse the batch
+        abort_batch(s, t.err, HKV_ERR_CUDA);
+        s.mflag[u] = 2;
+        continue;
+      }
+      g = b * kSlots + (uint64_t)slot;
+      t.sizes[b] = (n1 <= n2 ? n1 : n2) + 1u;
+    } else {
+      // D2: the bucket holding the lower minimum; admit iff (s, k) beats it
+      uint64_t s1, k1, s2 = ~0ull, k2 = ~0ull;
+      const int m1 = bucket_min(t, b1, s1, k1);
+      int m2 = -1;
+      if (two) m2 = bucket_min(t, b2, s2, k2);
+      const bool use2 = two && sk_less(s2, k2, s1, k1);
+      const uint64_t vs = use2 ? s2 : s1, vk = use2 ? k2 : k1;
+      if (sk_less(vs, vk, sc, key)) {
+        g = (use2 ? b2 : b1) * kSlots + (uint64_t)(use2 ? m2 : m1);
+        victim = vk;
+        vscore = vs;
+        if (s.evv) {
+          const float* vsrc = value_ptr(t, g);
+          for (uint32_t d = 0; d < t.dim; ++d) s.evv[u * t.dim + d] = __ldcg(vsrc + d);
+        }
+      }
+    }
+    s.evk[u] = victim;
+    if (g != ~0ull) {
+      s.evs[u] = vscore;
+      fill_slot_thread<VEC16, false>(t, g, key, sc, digest_from_hash(h), src);
+      s.tstatus[e] = HKV_ST_INSERTED;
+      if (victim == kEmptyKey) inserted++; else evicted++;
+    } else {
+      s.tstatus[e] = HKV_ST_REJECTED;
+      rejected++;
+    }
+    s.mflag[u] = 2;  // done; the reconcile pass reads its victim
+  }
+  const int which[3] = {HKV_CNT_INSERTED, HKV_CNT_EVICTED, HKV_CNT_REJECTED};
+  const unsigned vals[3] = {inserted, evicted, rejected};
+  flush_counts(t, which, vals);
+  const unsigned long long p = block_reserve(s.cnt + kCntPending, pending);
+  (void)p;
+}
+
 // --------------------------------------------------------------- reconcile
 
 constexpr int kRecThreads = 256;
@@ -854,8 +989,11 @@ hkv_status alloc_scratch(hkv_table_s* t, uint64_t n, bool upsert, bool want_ev_v
   const uint64_t sz_u64 = align256(n * 8);
   const uint64_t sz_cnt = align256(kCntWords * 8);
   const uint64_t sz_evv = want_ev_values ? align256(n * (uint64_t)t->dev.dim * 4) : 0;
+  // deterministic dual-bucket upserts run phase I in ordered waves
+  const bool ordered = upsert && t->opts.deterministic && t->dev.dual;
+  const uint64_t sz_owner = ordered ? align256(t->num_buckets * 8) : 0;
   uint64_t total = sz_tab + sz_ts + 2 * sz_u32 + sz_cnt + sz_u64;
-  if (upsert) total += sz_u8 + 2 * sz_u64 + 2 * sz_u32 + sz_evv;
+  if (upsert) total += sz_u8 + 2 * sz_u64 + 2 * sz_u32 + sz_evv + sz_owner;
   cudaError_t e = cudaMallocFromPoolAsync(&a->base, total, t->pool, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -879,6 +1017,9 @@ hkv_status alloc_scratch(hkv_table_s* t, uint64_t n, bool upsert, bool want_ev_v
     s.mi = reinterpret_cast<uint32_t*>(p); p += sz_u32;
     s.mm = reinterpret_cast<uint32_t*>(p); p += sz_u32;
     s.evv = want_ev_values ? reinterpret_cast<float*>(p) : nullptr;
+    p += sz_evv;
+    s.owner = ordered ? reinterpret_cast<unsigned long long*>(p) : nullptr;
+    if (ordered) cudaMemsetAsync(s.owner, 0, t->num_buckets * 8, st);
   }
   cudaMemsetAsync(s.tab, 0xFF, T * sizeof(DedupEntry), st);
   cudaMemsetAsync(s.cnt, 0, kCntWords * 8, st);
@@ -933,6 +1074,34 @@ void launch_dedup(hkv_table_s* t, uint64_t n, const uint64_t* keys, const Scratc
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// The waves of the ordered phase I, driven from the host: each wave's
+// pending count comes back before the next is launched, so the call returns
+// only after phase I has finished (the rest of the pipeline stays queued).
+hkv_status run_ordered_phase_i(hkv_table_s* t, uint64_t n, const Scratch& s, const float* values,
+                               const uint64_t* scores, ScoreCtx ctx, bool vec16,
+                               cudaStream_t st) {
+  KernelTimer timer(t->prof, HKV_K_INSERT, st);
+  const unsigned og = grid_for(t, n, kOrdThreads, 8);
+  for (uint64_t wave = 1;; ++wave) {
+    cudaMemsetAsync(s.cnt + kCntPending, 0, 8, st);
+    ordered_bid_kernel<<<og, kOrdThreads, 0, st>>>(t->dev, s, wave);
+    if (vec16)
+      ordered_insert_kernel<true><<<og, kOrdThreads, 0, st>>>(t->dev, s, values, scores, ctx,
+                                                               wave);
+    else
+      ordered_insert_kernel<false><<<og, kOrdThreads, 0, st>>>(t->dev, s, values, scores, ctx,
+                                                                wave);
+    cudaMemcpyAsync(t->host_word, s.cnt + kCntPending, 8, cudaMemcpyDeviceToHost, st);
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e, "ordered phase I");
+    if (*t->host_word == 0) return HKV_OK;
+    if (wave > n) {  // cannot happen: every wave places the smallest pending key
+      set_last_error("ordered phase I made no progress");
+      return HKV_ERR_TIMEOUT;
+    }
+  }
+}
+
 }  // namespace
 
 hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,
@@ -950,7 +1119,13 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
   const bool vec16 = t->dev.dim % 4 == 0 && aligned16(values);
   launch_dedup(t, n, keys, s, st);
   launch_update<true>(t, n, s, values, scores, ctx, vec16, st);
-  {
+  if (s.owner) {
+    rc = run_ordered_phase_i(t, n, s, values, scores, ctx, vec16, st);
+    if (rc) {
+      cudaFreeAsync(a.base, st);
+      return rc;
+    }
+  } else {
     const unsigned ig = grid_for(t, (n + 31) / 32 * 32, kInsThreads, kInsBlocksPerSm);
     KernelTimer timer(t->prof, HKV_K_INSERT, st);
     if (vec16)
@@ -1056,6 +1231,10 @@ hkv_status launch_upsert_in(hkv_table_s* t, uint64_t n, const uint64_t* keys, co
   if (n == 0) {
     if (n_evicted) cudaMemsetAsync(n_evicted, 0, 8, st);
     return cuda_status(cudaGetLastError(), "upsert");
+  }
+  if (t->opts.deterministic && t->dev.dual) {
+    set_last_error("deterministic dual-bucket tables take hkv_insert_or_assign only");
+    return HKV_ERR_INVALID_ARG;
   }
   Scratch s;
   if (!carve_scratch(scratch, scratch_bytes, n, &s)) {

@@ -332,3 +332,45 @@ def test_counters_account_for_every_key():
     c = t.read_counters()
     assert c["find_hit"] == int(np.sum(st == hkv.ST_INSERTED))
     assert c["find_hit"] + c["find_miss"] == keys.size
+
+
+@pytest.mark.parametrize("policy,dim", [(hkv.LFU, 32), (hkv.LRU, 8), (hkv.CUSTOM, 3),
+                                        (hkv.EPOCH_LFU, 4)])
+def test_deterministic_dual_bucket_bit_exact(policy, dim):
+    """Deterministic dual-bucket upsert runs phase I in batch order (waves of
+    keys with disjoint candidate buckets) and so equals Algorithm 3 run key
+    by key: statuses, evicted sets and the full state including the bucket
+    of every key, bit for bit, from an empty table through lambda = 1 and
+    well past it, with batches that mix resident and fresh keys."""
+    rng = np.random.default_rng(9500 + policy * 10 + dim)
+    nb = 256
+    t = hkv.Table(nb * 128, dim, policy, dual_bucket=True, deterministic=True)
+    o = oracle.OracleTable(nb, dim, policy, True)
+    sizes = [1, 0, 5000, 9000, 7001, 12000, 3, 8192, 10000, 6000, 9000, 2047]
+    for e, n in enumerate(sizes):
+        t.set_epoch(e)
+        o.set_epoch(e)
+        resident = o.export()[0]
+        k_old = rng.choice(resident, min(n // 3, resident.size), replace=False) if n else \
+            np.zeros(0, np.uint64)
+        k_new = w.uniform_keys(rng, n - k_old.size, distinct=True)
+        keys = np.concatenate([k_old, k_new]).astype(np.uint64)
+        assert np.unique(keys).size == keys.size
+        rng.shuffle(keys)
+        vals = w.normal_values(rng, keys.size, dim)
+        sc = rng.integers(0, 50, keys.size, dtype=np.uint64) if policy == hkv.CUSTOM else None
+        compare_upsert(t, o, keys, vals, sc, deterministic=True)
+        same_state(export_state(t), o.export())
+    assert o.size() == nb * 128  # filled, then evicting
+    q = np.concatenate([o.export()[0][:3000], w.uniform_keys(rng, 3000)])
+    compare_find(t, o, q)
+
+
+def test_deterministic_dual_tables_refuse_the_graph_and_noalloc_paths():
+    t = hkv.Table(128 * 16, 4, hkv.LRU, dual_bucket=True, deterministic=True)
+    with pytest.raises(hkv.HKVError):
+        hkv.Batch([t], [100])
+    keys = torch.arange(1, 11, dtype=torch.int64, device="cuda")
+    vals = torch.zeros((10, 4), device="cuda")
+    with pytest.raises(hkv.HKVError):
+        t.insert_or_assign_noalloc(keys, vals)
