@@ -62,7 +62,8 @@ def parse_args(argv=None):
                    help="skip the random-access ceiling measurement")
     p.add_argument("--find-tpk", type=int, default=0)
     p.add_argument("--update-tpk", type=int, default=0)
-    p.add_argument("--workload", choices=("single", "multi", "serve", "tiered"), default="single")
+    p.add_argument("--workload", choices=("single", "multi", "serve", "tiered", "ordered"),
+                   default="single")
     p.add_argument("--tiered-shrink", type=int, default=0,
                    help="divide the tiered table and its HBM budget by 2^k (small runs)")
     p.add_argument("--serve-budget-gib", type=float, default=120.0)
@@ -957,6 +958,85 @@ def run_serve(args):
             "peak": {"batched": peak_b, "plain": peak_p}, "served": served}
 
 
+def distinct_keys_torch(gen, n, universe, dev):
+    """n distinct keys of uniform ranks in [1, universe], in random order."""
+    import torch
+    from paper_2603_17168_gb300 import workloads as w
+    r = torch.unique(torch.randint(1, universe + 1, (n + n // 8 + 1024,), dtype=torch.int64,
+                                   device=dev, generator=gen))[:n]
+    return w.rank_to_key_torch(r[torch.randperm(r.numel(), device=dev, generator=gen)])
+
+
+def run_ordered(args):
+    """Deterministic dual-bucket upsert (ordered phase I) against the
+    concurrent mode on twin tables of the single-table shape, fed the same
+    duplicate-free batches (deterministic mode refuses duplicates): half the
+    keys of each batch come from the previous batch, half are fresh."""
+    import torch
+    import paper_2603_17168_gb300 as hkv
+    from paper_2603_17168_gb300 import workloads as w
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(w.seed_for(6))
+    nb, batch = 1 << args.nb_log2, args.batch
+    res = {}
+    for lam in (0.5, 1.0):
+        tabs = {m: hkv.Table(nb * 128, DIM, hkv.LFU, dual_bucket=True, deterministic=(m == "ordered"))
+                for m in ("ordered", "concurrent")}
+        target = lam * nb * 128 if lam < 1 else 0.999 * nb * 128
+        vals = torch.randn((batch, DIM), device=dev, generator=gen)
+        for _ in range(400):
+            if tabs["concurrent"].size() >= target:
+                break
+            k = distinct_keys_torch(gen, batch, UNIVERSE, dev)
+            for t in tabs.values():
+                t.insert_or_assign(k, vals[:k.numel()])
+        nbat = args.warmup + args.steps
+        prev = distinct_keys_torch(gen, batch, UNIVERSE, dev)
+        batches = []
+        for _ in range(nbat):
+            fresh = distinct_keys_torch(gen, batch, UNIVERSE, dev)
+            k = torch.unique(torch.cat([prev[:batch // 2], fresh[:batch // 2]]))
+            k = k[torch.randperm(k.numel(), device=dev, generator=gen)]
+            batches.append(k)
+            prev = k
+        st = torch.empty(batch, dtype=torch.uint8, device=dev)
+        row = {"lambda_fill": round(tabs["concurrent"].size() / (nb * 128), 4)}
+        for m, t in tabs.items():
+            for i in range(args.warmup):
+                t.insert_or_assign(batches[i], vals[:batches[i].numel()],
+                                   status_out=st[:batches[i].numel()])
+            torch.cuda.synchronize()
+            t.reset_counters()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            nk = 0
+            for i in range(args.warmup, nbat):
+                t.insert_or_assign(batches[i], vals[:batches[i].numel()],
+                                   status_out=st[:batches[i].numel()])
+                nk += batches[i].numel()
+            b.record()
+            b.synchronize()
+            c = t.read_counters()
+            row[m] = {"upsert_bkvs": round(nk / a.elapsed_time(b) / 1e6, 4),
+                      "updated": c["updated"], "inserted": c["inserted"],
+                      "evicted": c["evicted"], "rejected": c["rejected"]}
+        row["ordered_over_concurrent"] = round(row["ordered"]["upsert_bkvs"]
+                                               / row["concurrent"]["upsert_bkvs"], 4)
+        res[str(lam)] = row
+        for t in tabs.values():
+            t.close()
+    return {"metric": "insert_or_assign B-KV/s, deterministic (ordered phase I) vs concurrent "
+                      "dual-bucket", "value": res["1.0"]["ordered"]["upsert_bkvs"],
+            "unit": "B-KV/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"ordered: twin tables of {nb * 128} slots, dim {DIM}, LFU, "
+                                   f"dual-bucket; batches of {batch} distinct keys, half from "
+                                   "the previous batch, half fresh uniform over 2^32"},
+            "per_lambda": res}
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -973,6 +1053,10 @@ def main(argv=None):
         import __graft_entry__ as g
         g.build()
         res = run_serve(args)
+    elif args.workload == "ordered":
+        import __graft_entry__ as g
+        g.build()
+        res = run_ordered(args)
     else:
         import __graft_entry__ as g
         g.build()

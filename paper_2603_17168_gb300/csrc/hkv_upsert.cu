@@ -763,93 +763,130 @@ __global__ void __launch_bounds__(kOrdThreads)
   }
 }
 
-// Minimum (score, key) of a full bucket, read by one thread.
-__device__ __forceinline__ int bucket_min(const TableDev& t, uint64_t b, uint64_t& smin,
-                                          uint64_t& kmin) {
-  int m = -1;
-  smin = ~0ull;
-  kmin = ~0ull;
-  for (int j = 0; j < (int)kSlots; ++j) {
-    const uint64_t x = b * kSlots + (uint64_t)j;
-    const uint64_t sj = __ldcg(reinterpret_cast<const unsigned long long*>(t.scores) + x);
-    const uint64_t kj = __ldcg(reinterpret_cast<const unsigned long long*>(t.keys) + x);
-    if (m < 0 || sk_less(sj, kj, smin, kmin)) {
-      m = j;
-      smin = sj;
-      kmin = kj;
-    }
-  }
-  return m;
-}
-
+// A warp of the ordered phase I takes 32 consecutive u. Every lane checks
+// whether its key won both buckets this wave; winners with a free slot take
+// it alone (D1), winners whose candidates are full run the D2 victim search
+// as a warp, one key after another: coalesced (score, key) pairs of both
+// buckets, one warp argmin, admission, replacement. A winner owns its
+// buckets for the wave, so nothing here locks or re-checks.
 template <bool VEC16>
 __global__ void __launch_bounds__(kOrdThreads)
     ordered_insert_kernel(TableDev t, Scratch s, const float* __restrict__ values,
                           const uint64_t* __restrict__ scores_in, ScoreCtx ctx, uint64_t wave) {
   if (aborted(s)) return;
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * (uint64_t)kOrdThreads + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * kOrdThreads) >> 5;
   const uint64_t nu = s.cnt[kCntUnique];
   unsigned pending = 0, inserted = 0, evicted = 0, rejected = 0;
-  for (uint64_t u = blockIdx.x * (uint64_t)kOrdThreads + threadIdx.x; u < nu;
-       u += (uint64_t)gridDim.x * kOrdThreads) {
-    if (s.mflag[u] != 1) continue;
-    const uint64_t key = s.mkey[u];
-    const uint32_t i = s.mi[u], m = s.mm[u], e = s.ulist[u];
-    const uint64_t h = fmix64(key);
-    const uint64_t b1 = h & t.bucket_mask;
-    const uint64_t b2 = t.dual ? second_bucket(t, key) : b1;
-    const bool two = b2 != b1;
-    const unsigned long long tag = wave_tag(wave, i);
-    if (__ldcg(s.owner + b1) != tag || (two && __ldcg(s.owner + b2) != tag)) {
-      pending++;
-      continue;
-    }
-    const uint64_t sc = policy_score(t.policy, false, 0, m, scores_in != nullptr,
-                                     scores_in ? __ldg(scores_in + i) : 0, ctx);
-    const float* src = values + (uint64_t)i * t.dim;
-    const uint32_t n1 = __ldcg(t.sizes + b1);
-    const uint32_t n2 = two ? __ldcg(t.sizes + b2) : kSlots;
-    uint64_t g = ~0ull, victim = kEmptyKey, vscore = 0;
-    if (n1 < kSlots || n2 < kSlots) {
-      // D1: the less occupied candidate, b1 on equal occupancy
-      const uint64_t b = n1 <= n2 ? b1 : b2;
-      unsigned sectors = 0;
-      const int slot = find_free(t.digests + b * kSlots, 0u, sectors);
-      if (slot < 0) {  // a counter out of step with its digests: refuse the batch
-        abort_batch(s, t.err, HKV_ERR_CUDA);
-        s.mflag[u] = 2;
-        continue;
+  for (uint64_t c = warp; c * 32 < nu; c += nwarps) {
+    const uint64_t u = c * 32 + lane;
+    bool won = u < nu && s.mflag[u] == 1;
+    uint64_t key = 0, b1 = 0, b2 = 0, sc = 0;
+    uint32_t i = 0, e = 0, dg = 0;
+    bool full = false;
+    if (won) {
+      key = s.mkey[u];
+      i = s.mi[u];
+      e = s.ulist[u];
+      const uint64_t h = fmix64(key);
+      dg = digest_from_hash(h);
+      b1 = h & t.bucket_mask;
+      b2 = t.dual ? second_bucket(t, key) : b1;
+      const unsigned long long tag = wave_tag(wave, i);
+      if (__ldcg(s.owner + b1) != tag || (b2 != b1 && __ldcg(s.owner + b2) != tag)) {
+        pending++;
+        won = false;
       }
-      g = b * kSlots + (uint64_t)slot;
-      t.sizes[b] = (n1 <= n2 ? n1 : n2) + 1u;
-    } else {
-      // D2: the bucket holding the lower minimum; admit iff (s, k) beats it
-      uint64_t s1, k1, s2 = ~0ull, k2 = ~0ull;
-      const int m1 = bucket_min(t, b1, s1, k1);
-      int m2 = -1;
-      if (two) m2 = bucket_min(t, b2, s2, k2);
-      const bool use2 = two && sk_less(s2, k2, s1, k1);
-      const uint64_t vs = use2 ? s2 : s1, vk = use2 ? k2 : k1;
-      if (sk_less(vs, vk, sc, key)) {
-        g = (use2 ? b2 : b1) * kSlots + (uint64_t)(use2 ? m2 : m1);
-        victim = vk;
-        vscore = vs;
+    }
+    if (won) {
+      sc = policy_score(t.policy, false, 0, s.mm[u], scores_in != nullptr,
+                        scores_in ? __ldg(scores_in + i) : 0, ctx);
+      const uint32_t n1 = __ldcg(t.sizes + b1);
+      const uint32_t n2 = b2 != b1 ? __ldcg(t.sizes + b2) : kSlots;
+      if (n1 < kSlots || n2 < kSlots) {
+        // D1: the less occupied candidate, b1 on equal occupancy
+        const uint64_t b = n1 <= n2 ? b1 : b2;
+        unsigned sectors = 0;
+        const int slot = find_free(t.digests + b * kSlots, 0u, sectors);
+        if (slot < 0) {  // a counter out of step with its digests: refuse the batch
+          abort_batch(s, t.err, HKV_ERR_CUDA);
+        } else {
+          t.sizes[b] = (n1 <= n2 ? n1 : n2) + 1u;
+          fill_slot_thread<VEC16, false>(t, b * kSlots + (uint64_t)slot, key, sc, dg,
+                                         values + (uint64_t)i * t.dim);
+          s.evk[u] = kEmptyKey;
+          s.tstatus[e] = HKV_ST_INSERTED;
+          inserted++;
+        }
+        s.mflag[u] = 2;
+      } else {
+        full = true;
+      }
+    }
+    // D2, warp-cooperative, for the winners whose candidates are both full
+    unsigned todo = __ballot_sync(kFull, full);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint64_t uu = c * 32 + src;
+      const uint64_t k = __shfl_sync(kFull, key, src);
+      const uint64_t ks = __shfl_sync(kFull, sc, src);
+      const uint64_t c1 = __shfl_sync(kFull, b1, src), c2 = __shfl_sync(kFull, b2, src);
+      const uint32_t ki = __shfl_sync(kFull, i, src), ke = __shfl_sync(kFull, e, src);
+      const uint32_t kdg = __shfl_sync(kFull, dg, src);
+      const bool two = c2 != c1;
+      unsigned long long bs = ~0ull, bk = ~0ull;
+      int bq = -1;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        if (half == 1 && !two) break;
+        const uint64_t bb = half ? c2 : c1;
+        const ulonglong2* ps = reinterpret_cast<const ulonglong2*>(t.scores + bb * kSlots);
+        const ulonglong2* pk = reinterpret_cast<const ulonglong2*>(t.keys + bb * kSlots);
+        const ulonglong2 s0 = __ldcg(ps + lane), s1 = __ldcg(ps + 32 + lane);
+        const ulonglong2 k0 = __ldcg(pk + lane), k1 = __ldcg(pk + 32 + lane);
+        const unsigned long long sq[4] = {s0.x, s0.y, s1.x, s1.y};
+        const unsigned long long kq[4] = {k0.x, k0.y, k1.x, k1.y};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (sk_less(sq[j], kq[j], bs, bk)) {
+            bs = sq[j];
+            bk = kq[j];
+            bq = half * 4 + j;
+          }
+      }
+      unsigned long long smin, kmin;
+      bool at_min;
+      warp_min_sk(bs, bk, smin, kmin, at_min);
+      const int holder = __ffs(__ballot_sync(kFull, bq >= 0 && at_min)) - 1;
+      const uint64_t gl = (uint64_t)(bq < 4 ? c1 : c2) * kSlots + (uint64_t)held_slot(lane, bq & 3);
+      const uint64_t g = __shfl_sync(kFull, gl, holder);
+      if (sk_less(smin, kmin, ks, k)) {  // admitted: replace the minimum
         if (s.evv) {
           const float* vsrc = value_ptr(t, g);
-          for (uint32_t d = 0; d < t.dim; ++d) s.evv[u * t.dim + d] = __ldcg(vsrc + d);
+          for (uint32_t d = lane; d < t.dim; d += 32) s.evv[uu * t.dim + d] = __ldcg(vsrc + d);
         }
+        __syncwarp();
+        float* dst = value_ptr(t, g);
+        const float* vin = values + (uint64_t)ki * t.dim;
+        for (uint32_t d = lane; d < t.dim; d += 32) __stcg(dst + d, __ldg(vin + d));
+        if (lane == 0) {
+          t.digests[g] = (uint8_t)kdg;
+          __stcg(reinterpret_cast<unsigned long long*>(t.scores + g), (unsigned long long)ks);
+          __stcg(reinterpret_cast<unsigned long long*>(t.keys + g), (unsigned long long)k);
+          s.evk[uu] = kmin;
+          s.evs[uu] = smin;
+          s.tstatus[ke] = HKV_ST_INSERTED;
+          evicted++;
+        }
+      } else if (lane == 0) {
+        s.evk[uu] = kEmptyKey;
+        s.tstatus[ke] = HKV_ST_REJECTED;
+        rejected++;
       }
+      if (lane == 0) s.mflag[uu] = 2;
     }
-    s.evk[u] = victim;
-    if (g != ~0ull) {
-      s.evs[u] = vscore;
-      fill_slot_thread<VEC16, false>(t, g, key, sc, digest_from_hash(h), src);
-      s.tstatus[e] = HKV_ST_INSERTED;
-      if (victim == kEmptyKey) inserted++; else evicted++;
-    } else {
-      s.tstatus[e] = HKV_ST_REJECTED;
-      rejected++;
-    }
-    s.mflag[u] = 2;  // done; the reconcile pass reads its victim
   }
   const int which[3] = {HKV_CNT_INSERTED, HKV_CNT_EVICTED, HKV_CNT_REJECTED};
   const unsigned vals[3] = {inserted, evicted, rejected};
@@ -1074,28 +1111,34 @@ void launch_dedup(hkv_table_s* t, uint64_t n, const uint64_t* keys, const Scratc
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-// The waves of the ordered phase I, driven from the host: each wave's
-// pending count comes back before the next is launched, so the call returns
-// only after phase I has finished (the rest of the pipeline stays queued).
+// The waves of the ordered phase I, driven from the host: waves go out in
+// groups of kWavesPerCheck, and the last wave's pending count comes back
+// before the next group is launched (a wave with nothing pending costs two
+// short kernels; a host round trip per wave cost more). The call returns
+// only after phase I has finished; the rest of the pipeline stays queued.
+constexpr int kWavesPerCheck = 4;
+
 hkv_status run_ordered_phase_i(hkv_table_s* t, uint64_t n, const Scratch& s, const float* values,
                                const uint64_t* scores, ScoreCtx ctx, bool vec16,
                                cudaStream_t st) {
   KernelTimer timer(t->prof, HKV_K_INSERT, st);
   const unsigned og = grid_for(t, n, kOrdThreads, 8);
-  for (uint64_t wave = 1;; ++wave) {
-    cudaMemsetAsync(s.cnt + kCntPending, 0, 8, st);
-    ordered_bid_kernel<<<og, kOrdThreads, 0, st>>>(t->dev, s, wave);
-    if (vec16)
-      ordered_insert_kernel<true><<<og, kOrdThreads, 0, st>>>(t->dev, s, values, scores, ctx,
-                                                               wave);
-    else
-      ordered_insert_kernel<false><<<og, kOrdThreads, 0, st>>>(t->dev, s, values, scores, ctx,
-                                                                wave);
+  for (uint64_t wave = 1;; ) {
+    for (int k = 0; k < kWavesPerCheck; ++k, ++wave) {
+      cudaMemsetAsync(s.cnt + kCntPending, 0, 8, st);
+      ordered_bid_kernel<<<og, kOrdThreads, 0, st>>>(t->dev, s, wave);
+      if (vec16)
+        ordered_insert_kernel<true><<<og, kOrdThreads, 0, st>>>(t->dev, s, values, scores, ctx,
+                                                                 wave);
+      else
+        ordered_insert_kernel<false><<<og, kOrdThreads, 0, st>>>(t->dev, s, values, scores, ctx,
+                                                                  wave);
+    }
     cudaMemcpyAsync(t->host_word, s.cnt + kCntPending, 8, cudaMemcpyDeviceToHost, st);
     const cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_status(e, "ordered phase I");
     if (*t->host_word == 0) return HKV_OK;
-    if (wave > n) {  // cannot happen: every wave places the smallest pending key
+    if (wave > n + kWavesPerCheck) {  // cannot happen: each wave places the smallest pending key
       set_last_error("ordered phase I made no progress");
       return HKV_ERR_TIMEOUT;
     }
