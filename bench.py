@@ -473,6 +473,19 @@ def run_ours(args):
     for e in per_lambda:
         e.pop("_counters")
 
+    # find* (pointer-returning find) on the same tables and batches, after
+    # the timed region: value copy left out, as in the paper's find* numbers
+    ptrs = torch.empty(batch, dtype=torch.int64, device=dev)
+    for li, t in enumerate(tables):
+        t.find_ptr(fk[0], ptrs, out_f)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for i in range(warm, warm + steps):
+            t.find_ptr(fk[i], ptrs, out_f)
+        b.record()
+        b.synchronize()
+        per_lambda[li]["find_ptr_bkvs"] = round(steps * batch / a.elapsed_time(b) / 1e6, 4)
+
     # end to end through the public API: pinned host inputs copied in and
     # results copied out inside the timed region
     e2e = None

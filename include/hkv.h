@@ -125,6 +125,23 @@ uint64_t hkv_hbm_value_slots(hkv_table_t t); /* slots whose values sit in HBM */
 hkv_status hkv_find(hkv_table_t t, uint64_t n, const uint64_t *keys, float *values_out,
                     uint8_t *found, uint64_t *scores_out, hkv_stream_t stream);
 
+/* find* (reader; the pointer-returning find of Sec. 5.2 and Sec. 5.3): the
+ * probe of hkv_find, but a hit writes the address of its value row to
+ * ptrs_out[i] instead of copying the row, and a miss writes NULL. ptrs_out
+ * is a DEVICE array of n pointers; each is a device pointer into an HBM
+ * value slice or the device-mapped address of a host slice (position-based
+ * addressing, Sec. 3.6), 16-byte aligned when dim % 4 == 0. found may be
+ * NULL. An address stays valid until the next call that mutates the table
+ * (insert_or_assign, assign, erase) or destroys it. */
+hkv_status hkv_find_ptr(hkv_table_t t, uint64_t n, const uint64_t *keys, const float **ptrs_out,
+                        uint8_t *found, hkv_stream_t stream);
+
+/* Gather rows through pointers, the companion of find*: out[i] ([n][dim],
+ * DEVICE) = the dim floats at ptrs[i] (DEVICE array of n pointers); a NULL
+ * pointer leaves out[i] untouched. On the current device; asynchronous. */
+hkv_status hkv_gather_rows(const float *const *ptrs, uint64_t n, uint32_t dim, float *out,
+                           hkv_stream_t stream);
+
 /* contains (reader; Sec. 3.5): found[i] = 1 iff keys[i] is resident. */
 hkv_status hkv_contains(hkv_table_t t, uint64_t n, const uint64_t *keys, uint8_t *found,
                         hkv_stream_t stream);
@@ -206,6 +223,13 @@ hkv_status hkv_size(hkv_table_t t, uint64_t *out, hkv_stream_t stream);
 hkv_status hkv_export_batch(hkv_table_t t, uint64_t slot_offset, uint64_t n_slots,
                             uint64_t *count_out, uint64_t *keys, float *values,
                             uint64_t *scores, uint64_t *slots, hkv_stream_t stream);
+
+/* export_batch_if (reader; Sec. 4.1): hkv_export_batch restricted to the
+ * occupied slots whose score lies in [score_min, score_max] (inclusive). */
+hkv_status hkv_export_batch_if(hkv_table_t t, uint64_t slot_offset, uint64_t n_slots,
+                               uint64_t score_min, uint64_t score_max, uint64_t *count_out,
+                               uint64_t *keys, float *values, uint64_t *scores, uint64_t *slots,
+                               hkv_stream_t stream);
 
 /* Step and epoch used by the score policies (see hkv_policy). Host-side
  * state: apply to calls issued after this one. */

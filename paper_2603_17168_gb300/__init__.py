@@ -77,6 +77,9 @@ SIGNATURES = {
     "hkv_read_counters": (_i32, [_vp, _P64, _vp]),
     "hkv_reset_counters": (_i32, [_vp, _vp]),
     "hkv_set_launch": (_i32, [_vp, _i32, _i32]),
+    "hkv_find_ptr": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp]),
+    "hkv_gather_rows": (_i32, [_vp, _u64, _u32, _vp, _vp]),
+    "hkv_export_batch_if": (_i32, [_vp, _u64, _u64, _u64, _u64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hkv_set_l2_residency": (_i32, [_vp, _u64]),
     "hkv_l2_residency": (_u64, [_vp]),
     "hkv_batch_create": (_i32, [_i32, ctypes.POINTER(_vp), _P64, ctypes.POINTER(_vp)]),
@@ -215,6 +218,20 @@ class Table:
         _check(load_library().hkv_contains(self._h, n, _ptr(keys), _ptr(found), _stream(stream)))
         return found
 
+    def find_ptr(self, keys, ptrs=None, found=None, stream=None):
+        """find*: int64 tensor of value-row addresses (0 for misses), valid
+        until the next mutating call; read rows with gather_rows."""
+        import torch
+        n = keys.numel()
+        if ptrs is None:
+            ptrs = torch.empty(n, dtype=torch.int64, device=keys.device)
+        _need(keys, _u64_types(), (n,), "keys")
+        _need(ptrs, torch.int64, (n,), "ptrs")
+        _need(found, torch.uint8, (n,), "found")
+        _check(load_library().hkv_find_ptr(self._h, n, _ptr(keys), _ptr(ptrs), _ptr(found),
+                                           _stream(stream)))
+        return ptrs
+
     def size(self, stream=None) -> int:
         out = ctypes.c_uint64()
         _check(load_library().hkv_size(self._h, ctypes.byref(out), _stream(stream)))
@@ -233,6 +250,20 @@ class Table:
         _check(load_library().hkv_export_batch(self._h, slot_offset, n_slots, _ptr(count),
                                                _ptr(keys), _ptr(values), _ptr(scores),
                                                _ptr(slots), _stream(stream)))
+        return count, keys, values, scores, slots
+
+    def export_batch_if(self, score_min, score_max, slot_offset=0, n_slots=None, keys=None,
+                        values=None, scores=None, slots=None, count=None, stream=None):
+        """export_batch restricted to scores in [score_min, score_max]."""
+        import torch
+        if n_slots is None:
+            n_slots = self.capacity - slot_offset
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if count is None:
+            count = torch.zeros(1, dtype=torch.int64, device=dev)
+        _check(load_library().hkv_export_batch_if(
+            self._h, slot_offset, n_slots, int(score_min), int(score_max), _ptr(count),
+            _ptr(keys), _ptr(values), _ptr(scores), _ptr(slots), _stream(stream)))
         return count, keys, values, scores, slots
 
     # ------------------------------------------------------ updaters/inserters
@@ -415,6 +446,14 @@ class Batch:
             sc = o.get("scores")
             arr[i].scores = sc.data_ptr() if sc is not None else None
         _check(load_library().hkv_batch_run(self._h, arr, int(use_graph), _stream(stream)))
+
+
+def gather_rows(ptrs, dim, out, stream=None):
+    """out[i] = the dim floats at address ptrs[i] (int64 device tensor, e.g.
+    from Table.find_ptr); rows of zero addresses are left untouched."""
+    _check(load_library().hkv_gather_rows(_ptr(ptrs), ptrs.numel(), int(dim), _ptr(out),
+                                          _stream(stream)))
+    return out
 
 
 def measure_random_access(unit_bytes, write=False, buffer_bytes=8 << 30, accesses=64 << 20,

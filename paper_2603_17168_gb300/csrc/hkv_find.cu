@@ -8,6 +8,8 @@
 // the hit through one warp ballot. The hit's value row is then copied by the
 // same G lanes with 16-byte loads and streaming stores. Dual-bucket tables
 // read the second line only when the first bucket missed.
+#include <algorithm>
+
 #include "hkv_internal.h"
 
 namespace hkv {
@@ -19,7 +21,8 @@ template <int G, bool VEC16, bool VALUES>
 __global__ void __launch_bounds__(kFindThreads, 8)
     find_kernel(TableDev t, uint64_t n, const uint64_t* __restrict__ keys,
                 float* __restrict__ out, uint8_t* __restrict__ found,
-                uint64_t* __restrict__ scores_out, const OpDesc* __restrict__ d) {
+                uint64_t* __restrict__ scores_out, const OpDesc* __restrict__ d,
+                const float** __restrict__ ptrs_out) {
   if (d) {
     n = d->n;
     keys = d->keys;
@@ -67,6 +70,7 @@ __global__ void __launch_bounds__(kFindThreads, 8)
     }
     if (in && lane_g == 0) {
       if (found) found[i] = hit ? 1 : 0;
+      if (ptrs_out) ptrs_out[i] = hit ? value_ptr(t, b * kSlots + (uint64_t)slot) : nullptr;
       hits += hit;
       misses += !hit;
     }
@@ -79,7 +83,7 @@ __global__ void __launch_bounds__(kFindThreads, 8)
 template <int G>
 void launch_g(const hkv_table_s* t, uint64_t n, const uint64_t* keys, float* out, uint8_t* found,
               uint64_t* scores_out, bool vec16, cudaStream_t s, const OpDesc* d = nullptr,
-              bool values_if_desc = false) {
+              bool values_if_desc = false, const float** ptrs = nullptr) {
   const bool values = d ? values_if_desc : out != nullptr;
   uint64_t warps_needed = (n + (32 / G) - 1) / (32 / G);
   uint64_t blocks = (warps_needed * 32 + kFindThreads - 1) / kFindThreads;
@@ -88,13 +92,13 @@ void launch_g(const hkv_table_s* t, uint64_t n, const uint64_t* keys, float* out
   if (blocks == 0) blocks = 1;
   if (!values)
     launch_table_kernel(t, find_kernel<G, false, false>, (unsigned)blocks, kFindThreads, 0, s,
-                        t->dev, n, keys, out, found, scores_out, d);
+                        t->dev, n, keys, out, found, scores_out, d, ptrs);
   else if (vec16)
     launch_table_kernel(t, find_kernel<G, true, true>, (unsigned)blocks, kFindThreads, 0, s,
-                        t->dev, n, keys, out, found, scores_out, d);
+                        t->dev, n, keys, out, found, scores_out, d, ptrs);
   else
     launch_table_kernel(t, find_kernel<G, false, true>, (unsigned)blocks, kFindThreads, 0, s,
-                        t->dev, n, keys, out, found, scores_out, d);
+                        t->dev, n, keys, out, found, scores_out, d, ptrs);
 }
 
 }  // namespace
@@ -113,6 +117,59 @@ hkv_status launch_find(hkv_table_s* t, uint64_t n, const uint64_t* keys, float* 
     default: launch_g<8>(t, n, keys, values_out, found, scores_out, vec16, s); break;
   }
   return cuda_status(cudaGetLastError(), "find launch");
+}
+
+hkv_status launch_find_ptr(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float** ptrs,
+                           uint8_t* found, cudaStream_t s) {
+  if (n == 0) return HKV_OK;
+  KernelTimer timer(t->prof, HKV_K_FIND, s);
+  switch (t->launch.find_tpk) {
+    case 1: launch_g<1>(t, n, keys, nullptr, found, nullptr, false, s, nullptr, false, ptrs); break;
+    case 2: launch_g<2>(t, n, keys, nullptr, found, nullptr, false, s, nullptr, false, ptrs); break;
+    case 4: launch_g<4>(t, n, keys, nullptr, found, nullptr, false, s, nullptr, false, ptrs); break;
+    case 16:
+      launch_g<16>(t, n, keys, nullptr, found, nullptr, false, s, nullptr, false, ptrs);
+      break;
+    case 32:
+      launch_g<32>(t, n, keys, nullptr, found, nullptr, false, s, nullptr, false, ptrs);
+      break;
+    default: launch_g<8>(t, n, keys, nullptr, found, nullptr, false, s, nullptr, false, ptrs);
+  }
+  return cuda_status(cudaGetLastError(), "find* launch");
+}
+
+namespace {
+
+// Gather rows through pointers: one warp per row, 16-byte vectors when the
+// row and the output are 16-byte aligned. A null pointer leaves its row.
+__global__ void gather_rows_kernel(const float* const* __restrict__ ptrs, uint64_t n, uint32_t dim,
+                                   float* __restrict__ out, int vec16) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = warp; i < n; i += nwarps) {
+    const float* src = ptrs[i];
+    if (!src) continue;
+    float* dst = out + i * dim;
+    if (vec16) {
+      const float4* s4 = reinterpret_cast<const float4*>(src);
+      float4* d4 = reinterpret_cast<float4*>(dst);
+      for (uint32_t j = lane; j < dim / 4; j += 32) __stcs(d4 + j, __ldcg(s4 + j));
+    } else {
+      for (uint32_t j = lane; j < dim; j += 32) __stcs(dst + j, __ldcg(src + j));
+    }
+  }
+}
+
+}  // namespace
+
+hkv_status launch_gather(const float* const* ptrs, uint64_t n, uint32_t dim, float* out,
+                         int num_sms, cudaStream_t s) {
+  if (n == 0) return HKV_OK;
+  const uint64_t blocks = std::min<uint64_t>((n + 7) / 8, (uint64_t)num_sms * 8);
+  const int vec16 = dim % 4 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+  gather_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(ptrs, n, dim, out, vec16);
+  return cuda_status(cudaGetLastError(), "gather launch");
 }
 
 hkv_status launch_find_desc(hkv_table_s* t, uint64_t n_max, const OpDesc* d, bool values,

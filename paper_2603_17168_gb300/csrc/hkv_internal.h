@@ -163,6 +163,11 @@ hkv_status cuda_status(cudaError_t e, const char* what);
 // checking its launches.
 hkv_status launch_find(hkv_table_s* t, uint64_t n, const uint64_t* keys, float* values_out,
                        uint8_t* found, uint64_t* scores_out, cudaStream_t s);
+// find* (Sec. 5.2): value-row pointers instead of copies.
+hkv_status launch_find_ptr(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float** ptrs,
+                           uint8_t* found, cudaStream_t s);
+hkv_status launch_gather(const float* const* ptrs, uint64_t n, uint32_t dim, float* out,
+                         int num_sms, cudaStream_t s);
 hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,
                          const uint64_t* scores, uint8_t* status_out, uint64_t* ev_keys,
                          uint64_t* ev_scores, float* ev_values, uint64_t* n_evicted,
@@ -186,7 +191,7 @@ hkv_status launch_assign(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
 hkv_status launch_erase(hkv_table_s* t, uint64_t n, const uint64_t* keys, cudaStream_t s);
 hkv_status launch_export(hkv_table_s* t, uint64_t offset, uint64_t n_slots, uint64_t* count_out,
                          uint64_t* keys, float* values, uint64_t* scores, uint64_t* slots,
-                         cudaStream_t s);
+                         cudaStream_t s, uint64_t score_min = 0, uint64_t score_max = ~0ull);
 hkv_status launch_size(hkv_table_s* t, unsigned long long* out_dev, cudaStream_t s);
 
 }  // namespace hkv

@@ -49,7 +49,9 @@ __global__ void size_kernel(const uint8_t* __restrict__ digests, uint64_t n16,
 __global__ void export_kernel(TableDev t, uint64_t offset, uint64_t n_slots,
                               unsigned long long* count, uint64_t* __restrict__ keys,
                               float* __restrict__ values, uint64_t* __restrict__ scores,
-                              uint64_t* __restrict__ slots) {
+                              uint64_t* __restrict__ slots, uint64_t score_min,
+                              uint64_t score_max) {
+  const bool any_score = score_min == 0 && score_max == ~0ull;
   const int lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -57,7 +59,10 @@ __global__ void export_kernel(TableDev t, uint64_t offset, uint64_t n_slots,
     const uint64_t g = offset + base + lane;
     const bool in = base + lane < n_slots;
     const uint64_t k = in ? t.keys[g] : kEmptyKey;
-    const bool occ = in && k < kLockedKey;
+    bool occ = in && k < kLockedKey;
+    uint64_t sc = 0;
+    if (occ && (scores || !any_score)) sc = t.scores[g];
+    if (!any_score) occ = occ && sc >= score_min && sc <= score_max;
     const unsigned bal = __ballot_sync(0xFFFFFFFFu, occ);
     if (!bal) continue;
     unsigned long long o0 = 0;
@@ -66,7 +71,7 @@ __global__ void export_kernel(TableDev t, uint64_t offset, uint64_t n_slots,
     if (occ) {
       const unsigned long long o = o0 + __popc(bal & ((1u << lane) - 1u));
       if (keys) keys[o] = k;
-      if (scores) scores[o] = t.scores[g];
+      if (scores) scores[o] = sc;
       if (slots) slots[o] = g;
     }
     if (values) {
@@ -135,14 +140,14 @@ hkv_status launch_size(hkv_table_s* t, unsigned long long* out_dev, cudaStream_t
 
 hkv_status launch_export(hkv_table_s* t, uint64_t offset, uint64_t n_slots, uint64_t* count_out,
                          uint64_t* keys, float* values, uint64_t* scores, uint64_t* slots,
-                         cudaStream_t s) {
+                         cudaStream_t s, uint64_t score_min, uint64_t score_max) {
   cudaMemsetAsync(count_out, 0, 8, s);
   if (n_slots == 0) return cuda_status(cudaGetLastError(), "export");
   uint64_t blocks = std::min<uint64_t>((n_slots + 255) / 256, (uint64_t)t->num_sms * 8);
   KernelTimer timer(t->prof, HKV_K_EXPORT, s);
   export_kernel<<<(unsigned)std::max<uint64_t>(blocks, 1), 256, 0, s>>>(
       t->dev, offset, n_slots, reinterpret_cast<unsigned long long*>(count_out), keys, values,
-      scores, slots);
+      scores, slots, score_min, score_max);
   return cuda_status(cudaGetLastError(), "export launch");
 }
 
@@ -438,6 +443,40 @@ hkv_status hkv_export_batch(hkv_table_t t, uint64_t slot_offset, uint64_t n_slot
   hkv_status rc = launch_export(t, slot_offset, n_slots, count_out, keys, values, scores, slots, s);
   t->sched.release(s);
   return rc;
+}
+
+hkv_status hkv_export_batch_if(hkv_table_t t, uint64_t slot_offset, uint64_t n_slots,
+                               uint64_t score_min, uint64_t score_max, uint64_t* count_out,
+                               uint64_t* keys, float* values, uint64_t* scores, uint64_t* slots,
+                               hkv_stream_t stream) {
+  if (bad(t) || !count_out) return fail(HKV_ERR_INVALID_ARG, "export arguments");
+  if (slot_offset > t->capacity || n_slots > t->capacity - slot_offset)
+    return fail(HKV_ERR_INVALID_ARG, "slot range outside the table");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto lk = t->sched.acquire(kReader, s);
+  hkv_status rc = launch_export(t, slot_offset, n_slots, count_out, keys, values, scores, slots,
+                                s, score_min, score_max);
+  t->sched.release(s);
+  return rc;
+}
+
+hkv_status hkv_find_ptr(hkv_table_t t, uint64_t n, const uint64_t* keys, const float** ptrs_out,
+                        uint8_t* found, hkv_stream_t stream) {
+  if (bad(t) || (n && (!keys || !ptrs_out))) return fail(HKV_ERR_INVALID_ARG, "find* arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto lk = t->sched.acquire(kReader, s);
+  hkv_status rc = launch_find_ptr(t, n, keys, ptrs_out, found, s);
+  t->sched.release(s);
+  return rc;
+}
+
+hkv_status hkv_gather_rows(const float* const* ptrs, uint64_t n, uint32_t dim, float* out,
+                           hkv_stream_t stream) {
+  if ((n && (!ptrs || !out)) || dim == 0) return fail(HKV_ERR_INVALID_ARG, "gather arguments");
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return launch_gather(ptrs, n, dim, out, sms, static_cast<cudaStream_t>(stream));
 }
 
 hkv_status hkv_set_step(hkv_table_t t, uint64_t step) {

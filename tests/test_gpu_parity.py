@@ -374,3 +374,69 @@ def test_deterministic_dual_tables_refuse_the_graph_and_noalloc_paths():
     vals = torch.zeros((10, 4), device="cuda")
     with pytest.raises(hkv.HKVError):
         t.insert_or_assign_noalloc(keys, vals)
+
+
+@pytest.mark.parametrize("dim,budget_slices", [(16, None), (3, None), (8, 1)])
+def test_find_ptr_and_gather_bit_exact(dim, budget_slices):
+    """find* returns the address of each hit's value row: gathering through
+    the addresses gives exactly the oracle's rows, misses get NULL and keep
+    their output rows, distinct keys get distinct addresses. With a one-slice
+    HBM budget most rows live in mapped host memory."""
+    rng = np.random.default_rng(9700 + dim)
+    nb = 64
+    kw = {}
+    if budget_slices is not None:
+        kw = dict(hbm_value_budget_bytes=8 * 128 * dim * 4, slice_bytes=8 * 128 * dim * 4)
+    t = hkv.Table(nb * 128, dim, hkv.LFU, **kw)
+    o = oracle.OracleTable(nb, dim, oracle.LFU)
+    z = w.Zipf(1.05, 20000)
+    for n in (6000, 9000, 3000):
+        keys = z.keys(rng, n)
+        vals = w.normal_values(rng, n, dim)
+        compare_upsert(t, o, keys, vals)
+    q = np.concatenate([z.keys(rng, 4000), w.uniform_keys(rng, 2000), np.zeros(0, np.uint64)])
+    n = q.size
+    found = torch.empty(n, dtype=torch.uint8, device="cuda")
+    ptrs = t.find_ptr(dev(q), found=found)
+    out = nan_filled(n, dim)
+    hkv.gather_rows(ptrs, dim, out)
+    torch.cuda.synchronize()
+    ov = np.zeros((n, dim), np.uint32)
+    ov[:] = NAN_BITS
+    ov, of, _ = o.find(q, ov.view(np.float32))
+    p = host(ptrs).view(np.uint64)
+    gf = host(found).astype(bool)
+    assert np.array_equal(gf, of), "hit masks differ"
+    assert np.array_equal(p != 0, of), "NULL exactly for the misses"
+    assert np.array_equal(host(out).view(np.uint32), ov.view(np.uint32)), "rows differ"
+    hit_keys, first = np.unique(q[of], return_index=True)
+    assert np.unique(p[of][first]).size == hit_keys.size, "distinct keys share an address"
+    if dim % 4 == 0:
+        assert np.all(p[of] % 16 == 0)
+
+
+def test_export_batch_if_matches_filtered_export():
+    rng = np.random.default_rng(9800)
+    nb, dim = 64, 5
+    t = hkv.Table(nb * 128, dim, hkv.CUSTOM)
+    o = oracle.OracleTable(nb, dim, oracle.CUSTOM)
+    for n in (5000, 7000, 4000):
+        keys = w.uniform_keys(rng, n, distinct=True)
+        compare_upsert(t, o, keys, w.normal_values(rng, n, dim),
+                       rng.integers(0, 1000, n, dtype=np.uint64))
+    ok, os_, ov, ob = o.export()
+    cap = nb * 128
+    for lo, hi in ((0, 2**64 - 1), (100, 499), (500, 500), (1000, 2000), (0, 0)):
+        k = torch.empty(cap, dtype=torch.int64, device="cuda")
+        s = torch.empty(cap, dtype=torch.int64, device="cuda")
+        v = torch.empty((cap, dim), dtype=torch.float32, device="cuda")
+        cnt, *_ = t.export_batch_if(lo, hi, keys=k, values=v, scores=s)
+        torch.cuda.synchronize()
+        c = int(cnt.item())
+        gk, gs, gv = host(k[:c]), host(s[:c]), host(v[:c])
+        order = np.argsort(gk, kind="stable")
+        sel = (os_ >= lo) & (os_ <= hi)
+        assert c == int(sel.sum()), (lo, hi)
+        assert np.array_equal(gk[order], ok[sel])
+        assert np.array_equal(gs[order], os_[sel])
+        assert np.array_equal(gv[order].view(np.uint32), ov[sel].view(np.uint32))
