@@ -221,8 +221,8 @@ def traffic_for(kernel, workload_key):
 def kernel_bytes(kind: str, c: dict, n_calls: int, batch: int, dim: int) -> float:
     """Algorithmic bytes a kernel kind had to move, from the device counters.
     Coalesced streams count their exact bytes; each scattered scalar access
-    counts one 32-byte sector; a digest line is 128 B, a score line 1 KiB, a
-    value row 4*dim B (read and write counted separately)."""
+    counts one 32-byte sector; a digest line is 128 B, a bucket's (key, score)
+    run 2 KiB, a value row 4*dim B (read and write counted separately)."""
     D = 4 * dim
     S = 32
     if kind == "find":
@@ -242,8 +242,10 @@ def kernel_bytes(kind: str, c: dict, n_calls: int, batch: int, dim: int) -> floa
     if kind == "insert":
         ins = c["inserted"] - uc
         nm = ins + c["evicted"] + c["rejected"]
-        return (nm * (4 * 4 + S + S) + 128 * c["ins_lines"] + 1024 * c["ins_score_lines"]
-                + S * c["ins_keys"] + (ins + c["evicted"]) * (3 * S + 2 * D) + c["evicted"] * S)
+        # per search: the miss record, status and victim; one 2 KiB (key,
+        # score) run per candidate bucket per try; the slot written
+        return (nm * (4 * 4 + S + S) + 128 * c["ins_lines"] + 2048 * c["ins_score_lines"]
+                + (ins + c["evicted"]) * (3 * S + 2 * D) + c["evicted"] * S)
     if kind == "dedup":
         return n_calls * batch * (8 + 4) + u * 2 * S
     if kind == "status":

@@ -259,8 +259,9 @@ enum {
   HKV_CNT_UPD_KEYS = 11,   /* full keys read by the update phase */
   HKV_CNT_INS_LINES = 12,  /* digest lines read by the insert phase (0: free
                               slots are claimed in the update phase) */
-  HKV_CNT_INS_SCORES = 13, /* 1-KiB score lines read by victim searches */
-  HKV_CNT_INS_KEYS = 14,   /* keys read by victim searches (tie-break) */
+  HKV_CNT_INS_SCORES = 13, /* 2-KiB (key, score) pair runs read by victim
+                              searches (one per candidate bucket per try) */
+  HKV_CNT_INS_KEYS = 14,   /* 0: victim searches read keys with the pairs */
   HKV_CNT_TIMEOUT_FREE = 15,   /* free-slot claims that ran out of attempts */
   HKV_CNT_TIMEOUT_EVICT = 16,  /* victim searches that ran out of attempts */
   HKV_CNT_TIMEOUT_WHY = 17,    /* last such search's last failure: 1 a locked

@@ -2,8 +2,13 @@
 //
 // Table layout in HBM (Sec. 3.2, Fig. 4; Sec. 3.6; Sec. 4.2):
 //   digests [B][128] uint8   one 128-byte line per bucket; 0 = empty slot
-//   keys    [B][128] uint64  2^64-1 = empty, 2^64-2 = locked (slot CAS lock)
-//   scores  [B][128] uint64  the eviction metadata itself (Sec. 3.3)
+//   kv      [B][128][2] uint64  each slot's (key, score) as one 16-byte pair:
+//                            key 2^64-1 = empty, 2^64-2 = locked (slot CAS
+//                            lock); the score is the eviction metadata
+//                            itself (Sec. 3.3). A key confirmation brings the
+//                            score's sector along, a claim writes key and
+//                            score in one sector, and a victim search reads
+//                            one 2 KiB run per bucket.
 //   sizes   [B] uint32       occupied (or claimed) slots per bucket: the
 //                            dual-bucket choice reads two counters instead
 //                            of counting 256 digests
@@ -28,8 +33,7 @@ constexpr int kMaxClaimAttempts = 4096;             // bound on slot-claim retri
 
 struct TableDev {
   uint8_t* digests;
-  uint64_t* keys;
-  uint64_t* scores;
+  uint64_t* kv;              // [B][128] (key, score) pairs
   uint32_t* sizes;           // [B] slots claimed per bucket
   float* values0;            // slice 0 base
   float* const* slices;      // [n_slices] slice bases (device array)
@@ -89,6 +93,14 @@ __device__ __forceinline__ uint32_t digest_from_hash(uint64_t h) {
 
 __device__ __forceinline__ uint64_t second_bucket(const TableDev& t, uint64_t key) {
   return fmix64(key ^ kH2Salt) & t.bucket_mask;
+}
+
+// Key and score words of global slot g.
+__host__ __device__ __forceinline__ uint64_t* key_ptr(const TableDev& t, uint64_t g) {
+  return t.kv + 2 * g;
+}
+__host__ __device__ __forceinline__ uint64_t* score_ptr(const TableDev& t, uint64_t g) {
+  return t.kv + 2 * g + 1;
 }
 
 // ------------------------------------------------------------ value arena
@@ -247,7 +259,7 @@ __device__ __noinline__ int probe_rest(const uint8_t* line, const uint64_t* kb, 
       const int slot = first + q * 4 + (bit >> 3);
       m &= ~(0xFFu << (bit & ~7));
       if (slot == c0 || slot == c1 || slot == c2) continue;
-      const uint64_t k = CG ? __ldcg(kb + slot) : __ldg(kb + slot);
+      const uint64_t k = CG ? __ldcg(kb + 2 * slot) : __ldg(kb + 2 * slot);
       reads++;
       if (k == key) my = slot;
     }
@@ -281,14 +293,14 @@ __device__ __forceinline__ int probe_bucket(const TableDev& t, uint64_t b, uint6
   if (active && !TWO_PASS) {
     uint32_t w[W];
     load_line<G, CG>(t.digests + b * kSlots, lane_g, w);
-    const uint64_t* kb = t.keys + b * kSlots;
+    const uint64_t* kb = key_ptr(t, b * kSlots);  // key of slot j at kb[2 j]
 #pragma unroll
     for (int q = 0; q < W; ++q) {
       uint32_t m = match4(w[q], pat4);
       while (m) {
         const int bit = __ffs(m) - 1;
         const int slot = lane_g * (128 / G) + q * 4 + (bit >> 3);
-        const uint64_t k = CG ? __ldcg(kb + slot) : __ldg(kb + slot);
+        const uint64_t k = CG ? __ldcg(kb + 2 * slot) : __ldg(kb + 2 * slot);
         key_reads++;
         if (k == key) my = slot;
         m &= ~(0xFFu << (bit & ~7));
@@ -296,7 +308,7 @@ __device__ __forceinline__ int probe_bucket(const TableDev& t, uint64_t b, uint6
     }
   } else if (active) {
     const uint8_t* line = t.digests + b * kSlots;
-    const uint64_t* kb = t.keys + b * kSlots;
+    const uint64_t* kb = key_ptr(t, b * kSlots);  // key of slot j at kb[2 j]
     const int first = lane_g * (128 / G);
     int c0 = -1, c1 = -1, c2 = -1;
     bool more = false;
@@ -322,9 +334,9 @@ __device__ __forceinline__ int probe_bucket(const TableDev& t, uint64_t b, uint6
       }
     }
     uint64_t k0 = 0, k1 = 0, k2 = 0;
-    if (c0 >= 0) k0 = CG ? __ldcg(kb + c0) : __ldg(kb + c0);
-    if (c1 >= 0) k1 = CG ? __ldcg(kb + c1) : __ldg(kb + c1);
-    if (c2 >= 0) k2 = CG ? __ldcg(kb + c2) : __ldg(kb + c2);
+    if (c0 >= 0) k0 = CG ? __ldcg(kb + 2 * c0) : __ldg(kb + 2 * c0);
+    if (c1 >= 0) k1 = CG ? __ldcg(kb + 2 * c1) : __ldg(kb + 2 * c1);
+    if (c2 >= 0) k2 = CG ? __ldcg(kb + 2 * c2) : __ldg(kb + 2 * c2);
     key_reads += (c0 >= 0) + (c1 >= 0) + (c2 >= 0);
     if (c0 >= 0 && k0 == key) my = c0;
     else if (c1 >= 0 && k1 == key) my = c1;

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kFindThreads, 8)
     if (hit) {
       const uint64_t g = b * kSlots + (uint64_t)slot;
       if (VALUES) copy_row<G, VEC16, true>(out + i * t.dim, value_ptr(t, g), t.dim, lane_g);
-      if (scores_out && lane_g == 0) scores_out[i] = __ldg(t.scores + g);
+      if (scores_out && lane_g == 0) scores_out[i] = __ldg(score_ptr(t, g));
     }
     if (in && lane_g == 0) {
       if (found) found[i] = hit ? 1 : 0;

@@ -20,12 +20,10 @@ thread_local std::string g_last_error;
 
 constexpr uint64_t kDefaultSlice = 1ull << 30;
 
-__global__ void init_meta_kernel(uint8_t* digests, uint64_t* keys, uint64_t* scores,
-                                 uint64_t slots) {
+__global__ void init_meta_kernel(uint8_t* digests, uint64_t* kv, uint64_t slots) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < slots;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    keys[i] = kEmptyKey;
-    scores[i] = 0;
+    reinterpret_cast<ulonglong2*>(kv)[i] = make_ulonglong2(kEmptyKey, 0ull);
     if ((i & 15) == 0) reinterpret_cast<uint4*>(digests)[i >> 4] = make_uint4(0, 0, 0, 0);
   }
 }
@@ -58,10 +56,10 @@ __global__ void export_kernel(TableDev t, uint64_t offset, uint64_t n_slots,
   for (uint64_t base = warp * 32; base < n_slots; base += nwarps * 32) {
     const uint64_t g = offset + base + lane;
     const bool in = base + lane < n_slots;
-    const uint64_t k = in ? t.keys[g] : kEmptyKey;
+    const uint64_t k = in ? *key_ptr(t, g) : kEmptyKey;
     bool occ = in && k < kLockedKey;
     uint64_t sc = 0;
-    if (occ && (scores || !any_score)) sc = t.scores[g];
+    if (occ && (scores || !any_score)) sc = *score_ptr(t, g);
     if (!any_score) occ = occ && sc >= score_min && sc <= score_max;
     const unsigned bal = __ballot_sync(0xFFFFFFFFu, occ);
     if (!bal) continue;
@@ -212,10 +210,9 @@ hkv_status hkv_create(const hkv_options* o, hkv_table_t* out) {
   const uint64_t slots = t->capacity;
   const uint64_t dim = o->dim;
 
-  // metadata: digests | keys | scores | sizes | err | counters
-  const uint64_t off_keys = slots;                    // digests: slots bytes (multiple of 128)
-  const uint64_t off_scores = off_keys + slots * 8;
-  const uint64_t off_sizes = off_scores + slots * 8;
+  // metadata: digests | (key, score) pairs | sizes | err | counters
+  const uint64_t off_kv = slots;                      // digests: slots bytes (multiple of 128)
+  const uint64_t off_sizes = off_kv + slots * 16;
   const uint64_t off_err = off_sizes + ((nb * 4 + 255) & ~255ull);
   const uint64_t off_cnt = off_err + 256;
   const uint64_t meta_bytes = off_cnt + 256;
@@ -226,8 +223,7 @@ hkv_status hkv_create(const hkv_options* o, hkv_table_t* out) {
   }
   char* m = static_cast<char*>(t->meta);
   t->dev.digests = reinterpret_cast<uint8_t*>(m);
-  t->dev.keys = reinterpret_cast<uint64_t*>(m + off_keys);
-  t->dev.scores = reinterpret_cast<uint64_t*>(m + off_scores);
+  t->dev.kv = reinterpret_cast<uint64_t*>(m + off_kv);
   t->dev.sizes = reinterpret_cast<uint32_t*>(m + off_sizes);
   t->dev.err = reinterpret_cast<uint32_t*>(m + off_err);
   t->dev.counters = reinterpret_cast<unsigned long long*>(m + off_cnt);
@@ -304,8 +300,7 @@ hkv_status hkv_create(const hkv_options* o, hkv_table_t* out) {
     free_table(t);
     return cuda_status(e, "pinned word");
   }
-  init_meta_kernel<<<std::max(1, t->num_sms * 8), 256>>>(t->dev.digests, t->dev.keys,
-                                                         t->dev.scores, slots);
+  init_meta_kernel<<<std::max(1, t->num_sms * 8), 256>>>(t->dev.digests, t->dev.kv, slots);
   cudaMemset(t->dev.sizes, 0, nb * 4);
   cudaMemset(t->dev.err, 0, 256);
   cudaMemset(t->dev.counters, 0, 256);

@@ -258,7 +258,7 @@ template <bool VEC16, bool RELEASE>
 __device__ __forceinline__ void fill_slot_thread(const TableDev& t, uint64_t g, uint64_t key,
                                                  uint64_t sc, uint32_t dg, const float* src) {
   t.digests[g] = (uint8_t)dg;
-  __stcg(reinterpret_cast<unsigned long long*>(t.scores + g), (unsigned long long)sc);
+  __stcg(reinterpret_cast<unsigned long long*>(score_ptr(t, g)), (unsigned long long)sc);
   float* dst = value_ptr(t, g);
   if (VEC16) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
@@ -268,9 +268,9 @@ __device__ __forceinline__ void fill_slot_thread(const TableDev& t, uint64_t g, 
     for (uint32_t j = 0; j < t.dim; ++j) __stcg(dst + j, __ldg(src + j));
   }
   if (RELEASE)
-    publish_key(t.keys + g, key);
+    publish_key(key_ptr(t, g), key);
   else
-    __stcg(reinterpret_cast<unsigned long long*>(t.keys + g), (unsigned long long)key);
+    __stcg(reinterpret_cast<unsigned long long*>(key_ptr(t, g)), (unsigned long long)key);
 }
 
 // Back-off before retry `attempt` (> 0): exponential up to ~16 us, with
@@ -310,7 +310,7 @@ __device__ __forceinline__ uint8_t claim_free_slot(const TableDev& t, const Scra
       continue;
     }
     const uint64_t g = b * kSlots + (uint64_t)slot;
-    if (atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + g), kEmptyKey, kLockedKey) !=
+    if (atomicCAS(reinterpret_cast<unsigned long long*>(key_ptr(t, g)), kEmptyKey, kLockedKey) !=
         kEmptyKey) {
       retries++;
       continue;
@@ -340,7 +340,7 @@ __device__ __forceinline__ uint8_t claim_free_slot(const TableDev& t, const Scra
 __device__ __forceinline__ void update_resident_score(const TableDev& t, uint64_t g, uint64_t m,
                                                       bool have_caller, uint64_t caller,
                                                       const ScoreCtx& c) {
-  unsigned long long* p = reinterpret_cast<unsigned long long*>(t.scores + g);
+  unsigned long long* p = reinterpret_cast<unsigned long long*>(score_ptr(t, g));
   switch (t.policy) {
     case HKV_LFU:
       atomicAdd(p, (unsigned long long)m);
@@ -490,8 +490,8 @@ __device__ __forceinline__ void warp_min_sk(unsigned long long s, unsigned long 
   mine = tied;
 }
 
-// Slot of a bucket held by `lane` in the coalesced score layout: q = 0, 1
-// are slots 2*lane, 2*lane + 1; q = 2, 3 are 64 + 2*lane, 65 + 2*lane.
+// Slot of a bucket held by `lane` in a victim search's coalesced pair reads:
+// q = 0, 1 are slots 2*lane, 2*lane + 1; q = 2, 3 are 64 + 2*lane, 65 + 2*lane.
 __device__ __forceinline__ int held_slot(int lane, int q) {
   return (q >> 1) * 64 + 2 * lane + (q & 1);
 }
@@ -507,7 +507,7 @@ __device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_
                                           uint32_t dg, const float* src, int lane) {
   if (lane == 0) {
     t.digests[g] = (uint8_t)dg;
-    __stcg(reinterpret_cast<unsigned long long*>(t.scores + g), (unsigned long long)sc);
+    __stcg(reinterpret_cast<unsigned long long*>(score_ptr(t, g)), (unsigned long long)sc);
   }
   float* dst = value_ptr(t, g);
   if (VEC16) {
@@ -518,7 +518,7 @@ __device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_
     for (uint32_t j = lane; j < t.dim; j += 32) __stcg(dst + j, __ldg(src + j));
   }
   __syncwarp();
-  if (lane == 0) publish_key(t.keys + g, key);
+  if (lane == 0) publish_key(key_ptr(t, g), key);
   __syncwarp();
 }
 
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
   const uint64_t nu = s.cnt[kCntUnique];
   const uint64_t nchunks = (nu + 31) / 32;
   unsigned inserted = 0, evicted = 0, rejected = 0, retries = 0;
-  unsigned score_lines = 0, kreads = 0;
+  unsigned score_lines = 0;
 
   for (uint64_t c = warp; c < nchunks; c += nwarps) {
     // The chunk's 32 distinct keys: flags and miss records, coalesced.
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
     const bool full = my_flag == 2;
 
     // Warp-cooperative victim search for the keys whose buckets were
-    // full, one key after another. The score and key lines of the next
+    // full, one key after another. The (key, score) pair runs of the next
     // search are pulled into L2 by bulk prefetches while the current one
     // runs (deeper prefetching measured slower: it competes for L2 and
     // DRAM).
@@ -579,12 +579,8 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
         const int l = __ffs(ahead) - 1;
         ahead &= ahead - 1;
         if (lane == l) {
-          bulk_prefetch_l2(t.scores + my_b1 * kSlots, kSlots * 8);
-          bulk_prefetch_l2(t.keys + my_b1 * kSlots, kSlots * 8);
-          if (my_two) {
-            bulk_prefetch_l2(t.scores + my_b2 * kSlots, kSlots * 8);
-            bulk_prefetch_l2(t.keys + my_b2 * kSlots, kSlots * 8);
-          }
+          bulk_prefetch_l2(key_ptr(t, my_b1 * kSlots), kSlots * 16);
+          if (my_two) bulk_prefetch_l2(key_ptr(t, my_b2 * kSlots), kSlots * 16);
           if (VEC16) bulk_prefetch_l2(values + (uint64_t)my_i * t.dim, t.dim * 4);
         }
       }
@@ -599,12 +595,8 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
         if (ahead) {
           const int l = __ffs(ahead) - 1;
           if (lane == l) {
-            bulk_prefetch_l2(t.scores + my_b1 * kSlots, kSlots * 8);
-            bulk_prefetch_l2(t.keys + my_b1 * kSlots, kSlots * 8);
-            if (my_two) {
-              bulk_prefetch_l2(t.scores + my_b2 * kSlots, kSlots * 8);
-              bulk_prefetch_l2(t.keys + my_b2 * kSlots, kSlots * 8);
-            }
+            bulk_prefetch_l2(key_ptr(t, my_b1 * kSlots), kSlots * 16);
+            if (my_two) bulk_prefetch_l2(key_ptr(t, my_b2 * kSlots), kSlots * 16);
             if (VEC16) bulk_prefetch_l2(values + (uint64_t)my_i * t.dim, t.dim * 4);
           }
         }
@@ -628,8 +620,8 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
         if (attempt) claim_backoff(attempt, h);
         // Buckets stay full during a batch (no erase runs beside an
         // inserter), so the victim search needs no free-slot re-check.
-        // Each lane reads its slots' scores and keys as coalesced pairs
-        // (slots 2l, 2l+1 and 64+2l, 65+2l of each candidate bucket) and keeps
+        // Each lane reads its slots' (key, score) pairs, coalesced (slots
+        // 2l, 2l+1 and 64+2l, 65+2l of each candidate bucket) and keeps
         // its smallest (score, key); one warp argmin gives the victim. A slot
         // locked by another warp is mid-replacement: if its visible score
         // does not exceed the minimum, its next (score, key) could be the
@@ -641,12 +633,12 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
         for (int half = 0; half < 2; ++half) {
           if (half == 1 && !two) break;
           const uint64_t bb = half ? b2 : b1;
-          const ulonglong2* ps = reinterpret_cast<const ulonglong2*>(t.scores + bb * kSlots);
-          const ulonglong2* pk = reinterpret_cast<const ulonglong2*>(t.keys + bb * kSlots);
-          const ulonglong2 s0 = __ldcg(ps + lane), s1 = __ldcg(ps + 32 + lane);
-          const ulonglong2 k0 = __ldcg(pk + lane), k1 = __ldcg(pk + 32 + lane);
-          const unsigned long long sq[4] = {s0.x, s0.y, s1.x, s1.y};
-          const unsigned long long kq[4] = {k0.x, k0.y, k1.x, k1.y};
+          // (key, score) pairs of the held slots 2l, 2l+1, 64+2l, 65+2l
+          const ulonglong2* pp = reinterpret_cast<const ulonglong2*>(key_ptr(t, bb * kSlots));
+          const ulonglong2 p0 = __ldcg(pp + 2 * lane), p1 = __ldcg(pp + 2 * lane + 1);
+          const ulonglong2 p2 = __ldcg(pp + 64 + 2 * lane), p3 = __ldcg(pp + 65 + 2 * lane);
+          const unsigned long long sq[4] = {p0.y, p1.y, p2.y, p3.y};
+          const unsigned long long kq[4] = {p0.x, p1.x, p2.x, p3.x};
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             if (kq[j] >= kLockedKey) {
@@ -658,7 +650,6 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
             }
           }
         }
-        kreads += two ? 8 : 4;
         unsigned long long smin, kmin;
         bool mine;
         warp_min_sk(bs, bk, smin, kmin, mine);
@@ -682,11 +673,12 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
         if (lane == owner) {
           const uint64_t bqk = qbest < 4 ? b1 : b2;
           g = bqk * kSlots + (uint64_t)held_slot(lane, qbest & 3);
-          ok = atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + g), kmin, kLockedKey) == kmin;
+          ok = atomicCAS(reinterpret_cast<unsigned long long*>(key_ptr(t, g)), kmin,
+                         kLockedKey) == kmin;
           // A score and key read from two different occupants of the slot
           // would show here as a changed score: release and start over.
-          if (ok && __ldcg(reinterpret_cast<const unsigned long long*>(t.scores + g)) != smin) {
-            atomicExch(reinterpret_cast<unsigned long long*>(t.keys + g), kmin);
+          if (ok && __ldcg(reinterpret_cast<const unsigned long long*>(score_ptr(t, g))) != smin) {
+            atomicExch(reinterpret_cast<unsigned long long*>(key_ptr(t, g)), kmin);
             ok = 0;
             stale = 1;
           }
@@ -724,7 +716,7 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
   const int which[7] = {HKV_CNT_INSERTED, HKV_CNT_EVICTED, HKV_CNT_REJECTED, HKV_CNT_RETRIES,
                         HKV_CNT_INS_LINES, HKV_CNT_INS_SCORES, HKV_CNT_INS_KEYS};
   const unsigned vals[7] = {inserted, lane == 0 ? evicted : 0u, lane == 0 ? rejected : 0u,
-                            retries, 0u, lane == 0 ? score_lines : 0u, kreads};
+                            retries, 0u, lane == 0 ? score_lines : 0u, 0u};
   flush_counts(t, which, vals);
 }
 
@@ -842,12 +834,11 @@ __global__ void __launch_bounds__(kOrdThreads)
       for (int half = 0; half < 2; ++half) {
         if (half == 1 && !two) break;
         const uint64_t bb = half ? c2 : c1;
-        const ulonglong2* ps = reinterpret_cast<const ulonglong2*>(t.scores + bb * kSlots);
-        const ulonglong2* pk = reinterpret_cast<const ulonglong2*>(t.keys + bb * kSlots);
-        const ulonglong2 s0 = __ldcg(ps + lane), s1 = __ldcg(ps + 32 + lane);
-        const ulonglong2 k0 = __ldcg(pk + lane), k1 = __ldcg(pk + 32 + lane);
-        const unsigned long long sq[4] = {s0.x, s0.y, s1.x, s1.y};
-        const unsigned long long kq[4] = {k0.x, k0.y, k1.x, k1.y};
+        const ulonglong2* pp = reinterpret_cast<const ulonglong2*>(key_ptr(t, bb * kSlots));
+        const ulonglong2 p0 = __ldcg(pp + 2 * lane), p1 = __ldcg(pp + 2 * lane + 1);
+        const ulonglong2 p2 = __ldcg(pp + 64 + 2 * lane), p3 = __ldcg(pp + 65 + 2 * lane);
+        const unsigned long long sq[4] = {p0.y, p1.y, p2.y, p3.y};
+        const unsigned long long kq[4] = {p0.x, p1.x, p2.x, p3.x};
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           if (sk_less(sq[j], kq[j], bs, bk)) {
@@ -873,8 +864,8 @@ __global__ void __launch_bounds__(kOrdThreads)
         for (uint32_t d = lane; d < t.dim; d += 32) __stcg(dst + d, __ldg(vin + d));
         if (lane == 0) {
           t.digests[g] = (uint8_t)kdg;
-          __stcg(reinterpret_cast<unsigned long long*>(t.scores + g), (unsigned long long)ks);
-          __stcg(reinterpret_cast<unsigned long long*>(t.keys + g), (unsigned long long)k);
+          __stcg(reinterpret_cast<unsigned long long*>(score_ptr(t, g)), (unsigned long long)ks);
+          __stcg(reinterpret_cast<unsigned long long*>(key_ptr(t, g)), (unsigned long long)k);
           s.evk[uu] = kmin;
           s.evs[uu] = smin;
           s.tstatus[ke] = HKV_ST_INSERTED;
@@ -996,9 +987,9 @@ __global__ void __launch_bounds__(kUpdThreads)
       const uint64_t g = b * kSlots + (uint64_t)slot;
       // Duplicates of a key in one erase batch all find its slot: the CAS
       // lets exactly one of them clear it and count it out of its bucket.
-      if (atomicCAS(reinterpret_cast<unsigned long long*>(t.keys + g), key, kEmptyKey) == key) {
+      if (atomicCAS(reinterpret_cast<unsigned long long*>(key_ptr(t, g)), key, kEmptyKey) == key) {
         t.digests[g] = 0;
-        t.scores[g] = 0;
+        *score_ptr(t, g) = 0;
         atomicSub(t.sizes + b, 1u);
       }
     }
