@@ -56,6 +56,7 @@ def parse_args(argv=None):
     p.add_argument("--batch", type=int, default=BATCH)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--e2e-depth", type=int, default=8, help="staging slots of the e2e pipeline")
     p.add_argument("--l2-residency", action="store_true",
                    help="keep each table's digest array persisting in L2 (hkv_set_l2_residency)")
     p.add_argument("--no-random-access", action="store_true",
@@ -508,7 +509,7 @@ def run_ours(args):
     # results copied out inside the timed region
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(tables, fk, uk, uv, warm, steps, batch, world, dev)
+        e2e = run_e2e(tables, fk, uk, uv, warm, steps, batch, world, dev, args.e2e_depth)
     clk = clocks.summary(t_wall0, t_wall1)
     clocks.stop()
 
@@ -542,7 +543,7 @@ def run_ours(args):
     return result
 
 
-def run_e2e(tables, fk, uk, uv, warm, steps, batch, world, dev):
+def run_e2e(tables, fk, uk, uv, warm, steps, batch, world, dev, depth=3):
     """The same steps end to end through the library's host-buffer pipeline
     (hkv_pipeline_*): every step's keys and rows start in page-locked host
     memory and every result (find rows and flags, upsert statuses) ends
@@ -557,7 +558,7 @@ def run_e2e(tables, fk, uk, uv, warm, steps, batch, world, dev):
     ov_h = [torch.empty((batch, DIM)).pin_memory() for _ in tables]
     of_h = [torch.empty(batch, dtype=torch.uint8).pin_memory() for _ in tables]
     os_h = [torch.empty(batch, dtype=torch.uint8).pin_memory() for _ in tables]
-    pipe = hkv.Pipeline(batch, DIM, depth=3)
+    pipe = hkv.Pipeline(batch, DIM, depth=depth)
     h2d = d2h = 0
 
     def step(i, count):
@@ -585,7 +586,7 @@ def run_e2e(tables, fk, uk, uv, warm, steps, batch, world, dev):
             "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
             "ms_per_step": round(ms / steps, 4),
             "path": "hkv_pipeline_find / hkv_pipeline_insert_or_assign on page-locked host "
-                    "buffers, 3 staging slots"}
+                    f"buffers, {depth} staging slots"}
 
 
 # -------------------------------------------------------------- the oracle
