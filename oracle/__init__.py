@@ -86,6 +86,7 @@ def lib():
             "ot_insert_or_assign": (i32, [vp, u64, P64, PF, P64, i32, P8, P64, P64, PF, P64]),
             "ot_insert_or_assign_topk": (i32, [vp, u64, P64, PF, P64, i32, P8, P64, P64, PF, P64]),
             "ot_assign": (i32, [vp, u64, P64, PF, P64]),
+            "ot_find_or_insert": (i32, [vp, u64, P64, PF, P64, P8]),
             "ot_erase": (i32, [vp, u64, P64]),
             "ot_export": (u64, [vp, u64, P64, P64, PF, P64]),
             "ot_load": (i32, [vp, u64, P64, P64, PF, P64]),
@@ -210,6 +211,21 @@ class OracleTable:
     def insert_or_assign(self, keys, values, scores=None, deterministic=False):
         """Returns (status[n], evicted_keys, evicted_scores, evicted_values)."""
         return self._upsert(lib().ot_insert_or_assign, keys, values, scores, deterministic)
+
+    def find_or_insert(self, keys, values, scores=None):
+        """find_or_insert of a batch: returns (rows, found). rows[i] is the
+        key's value in the table afterwards, or values[i] if the table
+        refused the key; found[i] = 1 iff it was resident at batch start."""
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        n = keys.size
+        rows = np.ascontiguousarray(values, dtype=np.float32).reshape(n, self.dim).copy()
+        scores = None if scores is None else np.ascontiguousarray(scores, dtype=np.uint64)
+        found = np.zeros(n, np.uint8)
+        rc = lib().ot_find_or_insert(self._h, n, _u64p(keys), _f32p(rows), _u64p(scores),
+                                     _u8p(found))
+        if rc:
+            raise OracleError(rc)
+        return rows, found
 
     def insert_or_assign_topk(self, keys, values, scores=None, deterministic=False):
         """Closed-form single-bucket formulation (per-bucket top-S)."""

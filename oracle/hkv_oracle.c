@@ -11,7 +11,8 @@
  *   - Algorithm 2 (upsert with bucket-local admission and eviction), Sec. 3.3;
  *   - Algorithm 3 (score-based dual-bucket upsert), Sec. 3.4;
  *   - the reader / updater / inserter API roles of Sec. 3.5 (assign, erase,
- *     contains, size, export).
+ *     contains, size, export);
+ *   - find_or_insert, the cold-start primitive of Sec. 4.1.
  * Slot positions are not modelled: no observable result depends on them.
  *
  * Readings of points the paper leaves open (hash, digest bits, tie order,
@@ -465,6 +466,54 @@ int ot_insert_or_assign(ot_table *t, uint64_t n, const uint64_t *keys,
   finish_batch(t, u, nu, n, keys, status_out);
   if (n_evicted) *n_evicted = ev.n;
   free(u);
+  return OT_OK;
+}
+
+/* find_or_insert of a batch (the cold-start primitive of Sec. 4.1): a key
+ * resident at batch start keeps its value and has its score updated as an
+ * access (phase U without the value write); every other key is inserted
+ * with the value of its last occurrence under the same rules as
+ * insert_or_assign. Then each row of values_io becomes the key's value in
+ * the table, or stays the caller's row for a key the table refused;
+ * found_out[i] = 1 iff the key was resident at batch start. */
+int ot_find_or_insert(ot_table *t, uint64_t n, const uint64_t *keys, float *values_io,
+                      const uint64_t *scores, uint8_t *found_out) {
+  if (t->policy == OT_CUSTOM && !scores && n) return OT_ERR_INVALID_ARG;
+  int rc = validate_keys(n, keys);
+  if (rc) return rc;
+  if (n == 0) return OT_OK;
+  uint64_t nu;
+  uniq_t *u = dedup(n, keys, &nu);
+  if (!u) return OT_ERR_OOM;
+  t->step++;
+  phase_u(t, u, nu, NULL, scores);
+  evict_out ev = {NULL, NULL, NULL, 0};
+  for (uint64_t q = 0; q < nu; ++q) {
+    if (u[q].resident0) continue;
+    uint64_t s = policy_score(t, 0, 0, u[q].mult, scores != NULL,
+                              scores ? scores[u[q].last] : 0);
+    const float *v = values_io + u[q].last * t->dim;
+    if (t->dual)
+      upsert_dual(t, u[q].key, s, v, &ev);
+    else
+      upsert_single(t, bucket1(t, u[q].key), u[q].key, s, v, &ev);
+  }
+  if (found_out) {
+    qsort(u, nu, sizeof *u, cmp_uniq_key);
+    for (uint64_t i = 0; i < n; ++i) {
+      uniq_t probe = {keys[i], 0, 0, 0, 0};
+      uniq_t *hit = (uniq_t *)bsearch(&probe, u, nu, sizeof *u, cmp_uniq_key);
+      found_out[i] = hit->resident0 ? 1 : 0;
+    }
+  }
+  memset(t->fresh, 0, t->B * OT_S);
+  free(u);
+  /* rows from the table: every key resident now, in every occurrence */
+  for (uint64_t i = 0; i < n; ++i) {
+    uint64_t b; uint32_t j;
+    if (locate(t, keys[i], &b, &j))
+      memcpy(values_io + i * t->dim, t->values + at(b, j) * t->dim, t->dim * sizeof(float));
+  }
   return OT_OK;
 }
 
