@@ -199,6 +199,18 @@ hkv_status hkv_insert_or_assign_noalloc(hkv_table_t t, uint64_t n, const uint64_
                                         uint64_t *evicted_scores, uint64_t *n_evicted,
                                         hkv_stream_t stream);
 
+/* find_or_insert (inserter; the cold-start primitive of Sec. 4.1): a key
+ * resident at call start keeps its value and has its score updated as by
+ * hkv_insert_or_assign; every other key is inserted with the row of its last
+ * occurrence in values_io ([n][dim], DEVICE) under the rules of
+ * hkv_insert_or_assign (free slot, else admission against the minimum).
+ * Then every row of values_io whose key is resident becomes the stored
+ * value; rows of keys the table refused keep the caller's values.
+ * found_out[i] (nullable) = 1 iff keys[i] was resident at call start.
+ * Errors as in hkv_insert_or_assign. */
+hkv_status hkv_find_or_insert(hkv_table_t t, uint64_t n, const uint64_t *keys, float *values_io,
+                              const uint64_t *scores, uint8_t *found_out, hkv_stream_t stream);
+
 /* assign (updater; Sec. 3.5): for each resident key, overwrite its value
  * (last occurrence wins) and score per the policy; HKV_CUSTOM takes scores[]
  * when given, else keeps the old score. Missing keys are ignored; the bucket

@@ -78,6 +78,7 @@ SIGNATURES = {
     "hkv_reset_counters": (_i32, [_vp, _vp]),
     "hkv_set_launch": (_i32, [_vp, _i32, _i32]),
     "hkv_find_ptr": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp]),
+    "hkv_find_or_insert": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp, _vp]),
     "hkv_gather_rows": (_i32, [_vp, _u64, _u32, _vp, _vp]),
     "hkv_export_batch_if": (_i32, [_vp, _u64, _u64, _u64, _u64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hkv_set_l2_residency": (_i32, [_vp, _u64]),
@@ -231,6 +232,20 @@ class Table:
         _check(load_library().hkv_find_ptr(self._h, n, _ptr(keys), _ptr(ptrs), _ptr(found),
                                            _stream(stream)))
         return ptrs
+
+    def find_or_insert(self, keys, values_io, scores=None, found=None, stream=None):
+        """Rows of values_io become the stored values of resident keys
+        (missing keys are inserted with their rows first); returns found
+        (1 = resident at call start) if given."""
+        import torch
+        n = keys.numel()
+        _need(keys, _u64_types(), (n,), "keys")
+        _need(values_io, torch.float32, (n, self.dim), "values_io")
+        _need(scores, _u64_types(), (n,), "scores")
+        _need(found, torch.uint8, (n,), "found")
+        _check(load_library().hkv_find_or_insert(self._h, n, _ptr(keys), _ptr(values_io),
+                                                 _ptr(scores), _ptr(found), _stream(stream)))
+        return found
 
     def size(self, stream=None) -> int:
         out = ctypes.c_uint64()

@@ -171,7 +171,12 @@ hkv_status launch_gather(const float* const* ptrs, uint64_t n, uint32_t dim, flo
 hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,
                          const uint64_t* scores, uint8_t* status_out, uint64_t* ev_keys,
                          uint64_t* ev_scores, float* ev_values, uint64_t* n_evicted,
-                         ScoreCtx ctx, cudaStream_t s);
+                         ScoreCtx ctx, cudaStream_t s, bool keep_hits = false);
+// find_or_insert (Sec. 4.1): upsert that leaves residents' values alone,
+// then a find into values_io; found_out from the statuses.
+hkv_status launch_find_or_insert(hkv_table_s* t, uint64_t n, const uint64_t* keys,
+                                 float* values_io, const uint64_t* scores, uint8_t* found_out,
+                                 ScoreCtx ctx, cudaStream_t s);
 // The upsert pipeline run in a caller-provided scratch block of
 // scratch_bytes (device memory); no allocation. Evicted values not kept.
 hkv_status launch_upsert_in(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,

@@ -386,6 +386,24 @@ hkv_status hkv_insert_or_assign(hkv_table_t t, uint64_t n, const uint64_t* keys,
   return rc;
 }
 
+hkv_status hkv_find_or_insert(hkv_table_t t, uint64_t n, const uint64_t* keys, float* values_io,
+                              const uint64_t* scores, uint8_t* found_out, hkv_stream_t stream) {
+  if (bad(t) || (n && (!keys || !values_io)))
+    return fail(HKV_ERR_INVALID_ARG, "find_or_insert arguments");
+  if (n && t->opts.policy == HKV_CUSTOM && !scores)
+    return fail(HKV_ERR_INVALID_ARG, "HKV_CUSTOM needs scores");
+  if (n >= (1ull << 31)) return fail(HKV_ERR_INVALID_ARG, "batch above 2^31 keys");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto lk = t->sched.acquire(kInserter, s);
+  ScoreCtx ctx{n ? t->step + 1 : t->step, t->epoch};
+  hkv_status rc = launch_find_or_insert(t, n, keys, values_io,
+                                        (t->opts.policy == HKV_CUSTOM) ? scores : nullptr,
+                                        found_out, ctx, s);
+  if (rc == HKV_OK && n) t->step++;
+  t->sched.release(s);
+  return rc;
+}
+
 hkv_status hkv_assign(hkv_table_t t, uint64_t n, const uint64_t* keys, const float* values,
                       const uint64_t* scores, hkv_stream_t stream) {
   if (bad(t) || (n && !keys)) return fail(HKV_ERR_INVALID_ARG, "assign arguments");

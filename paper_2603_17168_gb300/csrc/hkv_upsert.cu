@@ -68,6 +68,7 @@ struct Scratch {
   const OpDesc* d;           // batched rounds: size, buffers and score context
   unsigned long long* owner; // [B] ordered phase I: (wave, ~batch index) of
                              // each bucket's first pending key, or null
+  int keep_hits;             // find_or_insert: residents keep their values
 };
 
 __device__ __forceinline__ uint64_t dedup_pos(uint64_t key, int bits) {
@@ -421,7 +422,8 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
     if (active) {
       if (hit) {
         const uint64_t g = b * kSlots + (uint64_t)slot;
-        if (values) copy_row<G, VEC16, false>(value_ptr(t, g), values + i * t.dim, t.dim, lane_g);
+        if (values && !s.keep_hits)
+          copy_row<G, VEC16, false>(value_ptr(t, g), values + i * t.dim, t.dim, lane_g);
         if (lane_g == 0) {
           update_resident_score(t, g, m, scores_in != nullptr, scores_in ? __ldg(scores_in + i) : 0,
                                 ctx);
@@ -1141,7 +1143,7 @@ hkv_status run_ordered_phase_i(hkv_table_s* t, uint64_t n, const Scratch& s, con
 hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,
                          const uint64_t* scores, uint8_t* status_out, uint64_t* ev_keys,
                          uint64_t* ev_scores, float* ev_values, uint64_t* n_evicted,
-                         ScoreCtx ctx, cudaStream_t st) {
+                         ScoreCtx ctx, cudaStream_t st, bool keep_hits) {
   if (n == 0) {
     if (n_evicted) cudaMemsetAsync(n_evicted, 0, 8, st);
     return cuda_status(cudaGetLastError(), "upsert");
@@ -1149,6 +1151,7 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
   ScratchAlloc a;
   hkv_status rc = alloc_scratch(t, n, true, ev_values != nullptr, st, &a);
   if (rc) return rc;
+  a.s.keep_hits = keep_hits ? 1 : 0;
   const Scratch& s = a.s;
   const bool vec16 = t->dev.dim % 4 == 0 && aligned16(values);
   launch_dedup(t, n, keys, s, st);
@@ -1353,6 +1356,38 @@ hkv_status launch_upsert_desc(hkv_table_s* t, uint64_t n_max, const OpDesc* d, v
                                                                              nullptr, nullptr);
   status_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(n, s, nullptr, nullptr);
   return cuda_status(cudaGetLastError(), "batched upsert launch");
+}
+
+}  // namespace hkv
+
+// ---------------------------------------------------------- find_or_insert
+
+namespace hkv {
+namespace {
+
+// found[i] = 1 iff the key was resident at batch start (status UPDATED).
+__global__ void status_to_found_kernel(uint64_t n, uint8_t* flags) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    flags[i] = flags[i] == HKV_ST_UPDATED ? 1 : 0;
+}
+
+}  // namespace
+
+hkv_status launch_find_or_insert(hkv_table_s* t, uint64_t n, const uint64_t* keys,
+                                 float* values_io, const uint64_t* scores, uint8_t* found_out,
+                                 ScoreCtx ctx, cudaStream_t st) {
+  // phase U without the value write, phase I as insert_or_assign (the
+  // caller's rows are the values of new keys), then every row of a key
+  // resident now is overwritten with its stored value
+  hkv_status rc = launch_upsert(t, n, keys, values_io, scores, found_out, nullptr, nullptr,
+                                nullptr, nullptr, ctx, st, true);
+  if (rc) return rc;
+  rc = launch_find(t, n, keys, values_io, nullptr, nullptr, st);
+  if (rc) return rc;
+  if (found_out && n)
+    status_to_found_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(n, found_out);
+  return cuda_status(cudaGetLastError(), "find_or_insert launch");
 }
 
 }  // namespace hkv

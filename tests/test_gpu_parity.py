@@ -440,3 +440,29 @@ def test_export_batch_if_matches_filtered_export():
         assert np.array_equal(gk[order], ok[sel])
         assert np.array_equal(gs[order], os_[sel])
         assert np.array_equal(gv[order].view(np.uint32), ov[sel].view(np.uint32))
+
+
+@pytest.mark.parametrize("policy,dual,det", [(hkv.LFU, False, False), (hkv.CUSTOM, False, False),
+                                             (hkv.LRU, True, True)])
+def test_find_or_insert_bit_exact(policy, dual, det):
+    """find_or_insert against the oracle's: returned rows, found flags and
+    the full state after every batch (Zipf batches with duplicates, or
+    distinct keys in deterministic dual-bucket mode), through the point
+    where the table is full and refuses keys."""
+    rng = np.random.default_rng(9900 + policy + 10 * dual)
+    nb, dim = 32, 4
+    t = hkv.Table(nb * 128, dim, policy, dual_bucket=dual, deterministic=det)
+    o = oracle.OracleTable(nb, dim, policy, dual)
+    z = w.Zipf(1.05, 12000)
+    for n in (3000, 0, 1, 5000, 7000, 4096):
+        keys = w.uniform_keys(rng, n, universe=12000, distinct=True) if det else z.keys(rng, n)
+        vals = w.normal_values(rng, n, dim)
+        sc = rng.integers(0, 40, n, dtype=np.uint64) if policy == hkv.CUSTOM else None
+        orows, ofound = o.find_or_insert(keys, vals, sc)
+        io = dev(vals.reshape(n, dim)) if n else torch.empty((0, dim), device="cuda")
+        found = torch.empty(n, dtype=torch.uint8, device="cuda")
+        t.find_or_insert(dev(keys), io, None if sc is None else dev(sc), found)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(found), ofound)
+        assert np.array_equal(host(io).view(np.uint32), orows.view(np.uint32))
+        same_state(export_state(t), o.export())
