@@ -63,8 +63,10 @@ def parse_args(argv=None):
                    help="skip the random-access ceiling measurement")
     p.add_argument("--find-tpk", type=int, default=0)
     p.add_argument("--update-tpk", type=int, default=0)
-    p.add_argument("--workload", choices=("single", "multi", "serve", "tiered", "ordered"),
-                   default="single")
+    p.add_argument("--workload", choices=("single", "multi", "serve", "tiered", "ordered",
+                                          "quality"), default="single")
+    p.add_argument("--quality-log2", type=int, default=27,
+                   help="log2 slots of the cache-quality tables")
     p.add_argument("--tiered-shrink", type=int, default=0,
                    help="divide the tiered table and its HBM budget by 2^k (small runs)")
     p.add_argument("--serve-budget-gib", type=float, default=120.0)
@@ -1069,6 +1071,112 @@ def run_ordered(args):
             "per_lambda": res}
 
 
+def quality_stream(t, policy_custom, z, gen, batch, n_batches, measure_from,
+                   track_first_eviction=False, keep=None):
+    """Sustained ingestion: per batch, look the keys up (contains), then
+    insert_or_assign them (scores = batch number for HKV_CUSTOM; the epoch
+    advances every batch). Returns (hits, lookups) over batches >=
+    measure_from and the load factor at the first eviction; `keep`, if
+    given, receives every batch's keys (for the stream's frequencies)."""
+    import torch
+    from paper_2603_17168_gb300 import workloads as w
+    dev = torch.device("cuda", 0)
+    vals = torch.zeros((batch, 1), device=dev)
+    hits = torch.zeros((), dtype=torch.int64, device=dev)
+    looked = 0
+    first_ev = None
+    for b in range(n_batches):
+        keys = w.zipf_keys_torch(gen, z, batch)
+        if keep is not None:
+            keep[b * batch:(b + 1) * batch] = keys
+        t.set_epoch(b)
+        if b >= measure_from:
+            hits += t.contains(keys).sum()
+            looked += batch
+        sc = torch.full((batch,), b, dtype=torch.int64, device=dev) if policy_custom else None
+        t.insert_or_assign(keys, vals, sc)
+        if track_first_eviction and first_ev is None:
+            c = t.read_counters()
+            if c["evicted"] + c["rejected"] > 0:
+                first_ev = t.size() / t.capacity
+    return int(hits.item()), looked, first_ev
+
+
+def run_quality(args):
+    """Cache quality under sustained Zipf ingestion (Sec. 5: Exp 3c, Exp 4).
+    Hit rate by policy and alpha: single-bucket tables of 2^quality_log2
+    slots, batches of 2^20 Zipf(alpha) keys over a universe of 2^30 and of
+    2^32 keys; the first two capacities of keys fill the table and reach
+    steady state, the hit rate is taken over the next three (5 x capacity in
+    all). Single vs dual bucket at alpha 0.99 under LFU (universe 2^30): the
+    load factor at the first eviction, the hit rate, and top-N retention: the
+    fraction of the N = capacity keys seen most often in the stream (ties by
+    the larger key, as the table breaks them) resident at the end."""
+    import torch
+    import paper_2603_17168_gb300 as hkv
+    from paper_2603_17168_gb300 import workloads as w
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    cap = 1 << args.quality_log2
+    batch = 1 << 20
+    per_cap = max(1, cap // batch)
+    n_batches, measure_from = 5 * per_cap, 2 * per_cap
+    policies = (("LRU", hkv.LRU), ("LFU", hkv.LFU), ("EPOCH_LRU", hkv.EPOCH_LRU),
+                ("EPOCH_LFU", hkv.EPOCH_LFU), ("CUSTOM", hkv.CUSTOM))
+    alphas = (0.5, 0.75, 0.99, 1.25)
+    hit_rate = {}
+    for ulog in (30, 32):
+        for alpha in alphas:
+            z = w.Zipf(alpha, 1 << ulog)
+            for name, pol in policies:
+                gen = torch.Generator(device=dev)
+                gen.manual_seed(w.seed_for(7) + int(alpha * 100) + ulog)  # one stream per (u, a)
+                t = hkv.Table(cap, 1, pol)
+                h, n, _ = quality_stream(t, pol == hkv.CUSTOM, z, gen, batch, n_batches,
+                                         measure_from)
+                hit_rate.setdefault(f"universe_2^{ulog}", {}).setdefault(name, {})[str(alpha)] = \
+                    round(100.0 * h / n, 2)
+                t.close()
+    z = w.Zipf(0.99, 1 << 30)
+    bucket = {}
+    for dual in (False, True):
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(w.seed_for(7) + 99)
+        t = hkv.Table(cap, 1, hkv.LFU, dual_bucket=dual)
+        seen = torch.empty(n_batches * batch, dtype=torch.int64, device=dev)
+        h, n, first = quality_stream(t, False, z, gen, batch, n_batches, measure_from,
+                                     track_first_eviction=True, keep=seen)
+        k = torch.empty(cap, dtype=torch.int64, device=dev)
+        cnt, *_ = t.export_batch(0, cap, keys=k)
+        torch.cuda.synchronize()
+        resident = torch.sort(k[:int(cnt.item())])[0]
+        uk, counts = torch.unique(seen, return_counts=True)
+        del seen
+        # the N keys seen most often, ties by the larger key: order by
+        # (count, key) descending
+        o = torch.sort(uk, descending=True, stable=True)[1]
+        o = o[torch.sort(counts[o], descending=True, stable=True)[1]]
+        ideal = uk[o[:cap]]
+        j = torch.searchsorted(resident, ideal).clamp_(max=max(resident.numel() - 1, 0))
+        retained = int((resident[j] == ideal).sum().item())
+        bucket["dual" if dual else "single"] = {
+            "first_eviction_lambda": round(first, 4) if first is not None else None,
+            "top_n_retention_pct": round(100.0 * retained / min(cap, ideal.numel()), 2),
+            "hit_rate_pct": round(100.0 * h / n, 2)}
+        t.close()
+    return {"metric": "cache hit rate (%) by policy and Zipf alpha; single vs dual bucket",
+            "value": hit_rate["universe_2^30"]["LFU"]["0.99"],
+            "unit": "% hit rate (LFU, alpha 0.99, universe 2^30)",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"quality: {cap} slots, dim 1, batches of {batch} Zipf(alpha) "
+                                   "keys over 2^30 and 2^32; per batch contains() then "
+                                   "insert_or_assign; 2 capacities of warm-up, hit rate over the "
+                                   "next 3; HKV_CUSTOM scores = batch number; epoch = batch "
+                                   "number; top-N = the capacity keys seen most often",
+                       "capacity": cap, "batch": batch},
+            "hit_rate_pct": hit_rate, "single_vs_dual_alpha_0.99_lfu_universe_2^30": bucket}
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -1089,6 +1197,10 @@ def main(argv=None):
         import __graft_entry__ as g
         g.build()
         res = run_ordered(args)
+    elif args.workload == "quality":
+        import __graft_entry__ as g
+        g.build()
+        res = run_quality(args)
     else:
         import __graft_entry__ as g
         g.build()

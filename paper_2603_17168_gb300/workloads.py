@@ -122,6 +122,14 @@ def rank_to_key_torch(ranks):
     return (ranks.to(torch.int64) * g) & ((1 << 63) - 1)
 
 
+def key_to_rank_torch(keys):
+    """Inverse of rank_to_key_torch: the rank of each key (mod 2^63)."""
+    import torch
+    inv = pow(int(GOLDEN), -1, 1 << 63)  # < 2^63: fits an int64
+    g = torch.tensor(inv, dtype=torch.int64, device=keys.device)
+    return (keys.to(torch.int64) * g) & ((1 << 63) - 1)
+
+
 def uniform_keys_torch(gen, n: int, universe: int, device="cuda"):
     import torch
     r = torch.randint(1, universe + 1, (n,), dtype=torch.int64, device=device, generator=gen)
