@@ -64,7 +64,7 @@ def parse_args(argv=None):
     p.add_argument("--find-tpk", type=int, default=0)
     p.add_argument("--update-tpk", type=int, default=0)
     p.add_argument("--workload", choices=("single", "multi", "serve", "tiered", "ordered",
-                                          "quality"), default="single")
+                                          "quality", "concurrency"), default="single")
     p.add_argument("--quality-log2", type=int, default=27,
                    help="log2 slots of the cache-quality tables")
     p.add_argument("--tiered-shrink", type=int, default=0,
@@ -1177,6 +1177,85 @@ def run_quality(args):
             "hit_rate_pct": hit_rate, "single_vs_dual_alpha_0.99_lfu_universe_2^30": bucket}
 
 
+def run_concurrency(args):
+    """Concurrency ablation (Sec. 5, Exp 3e): host client threads, each with
+    its own CUDA stream, issue 200 batches of 2^16 keys of one role (find,
+    assign, or insert_or_assign of fresh keys) against one table (2^24 slots,
+    dim 16, LRU, filled to lambda 0.75), under the triple-group rule and
+    under a reader/writer lock (hkv_set_concurrency). Throughput = all keys
+    / wall time from the start barrier to the last stream's completion."""
+    import threading
+    import torch
+    import paper_2603_17168_gb300 as hkv
+    from paper_2603_17168_gb300 import workloads as w
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    cap, dim, batch, nbat, pool = 1 << 24, 16, 1 << 16, 200, 8
+    mixes = {"1U": (0, 1, 0), "2U": (0, 2, 0), "4U": (0, 4, 0), "10U": (0, 10, 0),
+             "4F/5U/1I": (4, 5, 1), "4F/2U/4I": (4, 2, 4), "8F/1U/1I": (8, 1, 1)}
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(w.seed_for(8))
+    res = {}
+    for mix, (nf, nu, ni) in mixes.items():
+        row = {}
+        for mode in ("triple_group", "rw_lock"):
+            t = hkv.Table(cap, dim, hkv.LRU)
+            fill = torch.randn((1 << 20, dim), device=dev, generator=gen)
+            while t.size() < 0.75 * cap:
+                t.insert_or_assign(w.uniform_keys_torch(gen, 1 << 20, 1 << 40), fill)
+            k = torch.empty(cap, dtype=torch.int64, device=dev)
+            cnt, *_ = t.export_batch(0, cap, keys=k)
+            torch.cuda.synchronize()
+            resident = k[:int(cnt.item())]
+            t.set_concurrency(mode == "rw_lock")
+            roles = ["F"] * nf + ["U"] * nu + ["I"] * ni
+            work = []
+            for r in roles:
+                if r == "I":
+                    keys = [w.uniform_keys_torch(gen, batch, 1 << 40) for _ in range(pool)]
+                else:
+                    keys = [resident[torch.randint(0, resident.numel(), (batch,), device=dev,
+                                                   generator=gen)] for _ in range(pool)]
+                vals = [torch.randn((batch, dim), device=dev, generator=gen) for _ in range(pool)]
+                out = torch.empty((batch, dim), device=dev)
+                work.append((r, keys, vals, out, torch.cuda.Stream()))
+            torch.cuda.synchronize()
+            start = threading.Barrier(len(work) + 1)
+
+            def client(r, keys, vals, out, s):
+                start.wait()
+                for i in range(nbat):
+                    if r == "F":
+                        t.find(keys[i % pool], out, stream=s)
+                    elif r == "U":
+                        t.assign(keys[i % pool], vals[i % pool], stream=s)
+                    else:
+                        t.insert_or_assign(keys[i % pool], vals[i % pool], stream=s)
+                s.synchronize()
+
+            th = [threading.Thread(target=client, args=wk) for wk in work]
+            for x in th:
+                x.start()
+            start.wait()
+            t0 = time.perf_counter()
+            for x in th:
+                x.join()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            row[mode] = round(len(work) * nbat * batch / dt / 1e9, 4)
+            t.close()
+        row["triple_over_rw"] = round(row["triple_group"] / row["rw_lock"], 3)
+        res[mix] = row
+    return {"metric": "B-KV/s under concurrent host clients: triple-group vs reader/writer lock",
+            "value": res["10U"]["triple_group"], "unit": "B-KV/s (10 updater threads)",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"concurrency: one table of {cap} slots, dim {dim}, LRU, "
+                                   f"lambda 0.75; client threads with their own streams, {nbat} "
+                                   f"batches of {batch} keys each (F find, U assign of resident "
+                                   "keys, I insert_or_assign of fresh keys)"},
+            "mixes": res}
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -1201,6 +1280,10 @@ def main(argv=None):
         import __graft_entry__ as g
         g.build()
         res = run_quality(args)
+    elif args.workload == "concurrency":
+        import __graft_entry__ as g
+        g.build()
+        res = run_concurrency(args)
     else:
         import __graft_entry__ as g
         g.build()

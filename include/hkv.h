@@ -295,6 +295,15 @@ hkv_status hkv_reset_counters(hkv_table_t t, hkv_stream_t stream);
  * these; defaults follow the value width. */
 hkv_status hkv_set_launch(hkv_table_t t, int find_threads_per_key, int update_threads_per_key);
 
+/* Concurrency rule between calls on different streams (Sec. 3.5, Table 4).
+ * HKV_CC_TRIPLE_GROUP (default): readers run beside readers and updaters
+ * beside updaters, every other pair is ordered. HKV_CC_RW_LOCK: the
+ * conventional reader/writer lock of the paper's Exp 3e, where updaters
+ * are writers and are ordered among themselves as well. Applies to calls
+ * issued afterwards. */
+enum { HKV_CC_TRIPLE_GROUP = 0, HKV_CC_RW_LOCK = 1 };
+hkv_status hkv_set_concurrency(hkv_table_t t, int mode);
+
 /* L2 residency of the digest array (no counterpart in the paper; the
  * GB300's 126 MB L2 holds the whole digest array of a table up to 2^26
  * slots). Every probe reads a bucket's 128-byte digest line before anything

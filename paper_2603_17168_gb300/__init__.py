@@ -82,6 +82,7 @@ SIGNATURES = {
     "hkv_gather_rows": (_i32, [_vp, _u64, _u32, _vp, _vp]),
     "hkv_export_batch_if": (_i32, [_vp, _u64, _u64, _u64, _u64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hkv_set_l2_residency": (_i32, [_vp, _u64]),
+    "hkv_set_concurrency": (_i32, [_vp, _i32]),
     "hkv_l2_residency": (_u64, [_vp]),
     "hkv_batch_create": (_i32, [_i32, ctypes.POINTER(_vp), _P64, ctypes.POINTER(_vp)]),
     "hkv_batch_run": (_i32, [_vp, ctypes.POINTER(BatchOp), _i32, _vp]),
@@ -373,6 +374,10 @@ class Table:
     def set_launch(self, find_threads_per_key: int = 0, update_threads_per_key: int = 0):
         _check(load_library().hkv_set_launch(self._h, find_threads_per_key,
                                              update_threads_per_key))
+
+    def set_concurrency(self, rw_lock: bool):
+        """Triple-group rule (default) or a reader/writer lock (Exp 3e)."""
+        _check(load_library().hkv_set_concurrency(self._h, 1 if rw_lock else 0))
 
     def set_l2_residency(self, digest_bytes: int):
         """Bytes of the digest array kept persisting in L2 (0: off)."""

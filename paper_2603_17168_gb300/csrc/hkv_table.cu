@@ -321,6 +321,13 @@ hkv_status hkv_create(const hkv_options* o, hkv_table_t* out) {
   return HKV_OK;
 }
 
+hkv_status hkv_set_concurrency(hkv_table_t t, int mode) {
+  if (bad(t) || (mode != HKV_CC_TRIPLE_GROUP && mode != HKV_CC_RW_LOCK))
+    return fail(HKV_ERR_INVALID_ARG, "concurrency mode");
+  t->sched.set_rw_lock(mode == HKV_CC_RW_LOCK);
+  return HKV_OK;
+}
+
 hkv_status hkv_set_l2_residency(hkv_table_t t, uint64_t digest_bytes) {
   if (bad(t)) return fail(HKV_ERR_INVALID_ARG, "null table");
   int dev = 0;

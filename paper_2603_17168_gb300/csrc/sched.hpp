@@ -29,7 +29,12 @@ namespace hkv {
 
 enum Group : int { kReader = 0, kUpdater = 1, kInserter = 2 };
 
-inline bool compatible(Group a, Group b) { return a == b && a != kInserter; }
+// Table 4: readers with readers, updaters with updaters, all else exclusive.
+// rw_lock: the conventional reader/writer lock the paper compares against
+// (Exp 3e), where updaters are writers and exclude each other too.
+inline bool compatible(Group a, Group b, bool rw_lock = false) {
+  return a == b && a != kInserter && !(rw_lock && a == kUpdater);
+}
 
 template <class Backend>
 class TripleGroup {
@@ -44,7 +49,7 @@ class TripleGroup {
   // Call with the returned lock held until release().
   std::unique_lock<std::mutex> acquire(Group g, Stream s) {
     std::unique_lock<std::mutex> lk(mu_);
-    if (!(have_epoch_ && compatible(group_, g))) {
+    if (!(have_epoch_ && compatible(group_, g, rw_lock_))) {
       for (auto& fe : frontier_) be_.recycle(fe.second);
       frontier_ = std::move(current_);
       current_.clear();
@@ -80,10 +85,18 @@ class TripleGroup {
 
   Backend& backend() { return be_; }
 
+  // Switch between the triple-group rule and a reader/writer lock; takes
+  // effect for operations acquired afterwards.
+  void set_rw_lock(bool on) {
+    std::lock_guard<std::mutex> lk(mu_);
+    rw_lock_ = on;
+  }
+
  private:
   Backend be_;
   std::mutex mu_;
   bool have_epoch_ = false;
+  bool rw_lock_ = false;
   Group group_ = kReader;
   std::vector<std::pair<Stream, Event>> frontier_;
   std::vector<std::pair<Stream, Event>> current_;

@@ -27,15 +27,27 @@ struct SimEvents {
 
 extern "C" {
 
+int hkv_sched_sim_mode(int n_ops, const int* group, const int* stream, const double* issue,
+                       const double* dur, int n_streams, int rw_lock, double* start,
+                       double* end);
+
 // Run ops in issue order: op i of group[i] (0 reader, 1 updater, 2 inserter)
 // on stream[i], issued by the host at issue[i], lasting dur[i]. Writes each
 // op's start and end on the virtual clock. Returns 0, or -1 on bad input.
 int hkv_sched_sim(int n_ops, const int* group, const int* stream, const double* issue,
                   const double* dur, int n_streams, double* start, double* end) {
+  return hkv_sched_sim_mode(n_ops, group, stream, issue, dur, n_streams, 0, start, end);
+}
+
+// As hkv_sched_sim, with rw_lock = 1 for the reader/writer-lock rule.
+int hkv_sched_sim_mode(int n_ops, const int* group, const int* stream, const double* issue,
+                       const double* dur, int n_streams, int rw_lock, double* start,
+                       double* end) {
   if (n_ops < 0 || n_streams <= 0) return -1;
   SimEvents be;
   be.ready.assign(n_streams, 0.0);
   hkv::TripleGroup<SimEvents> tg(be);
+  tg.set_rw_lock(rw_lock != 0);
   for (int i = 0; i < n_ops; ++i) {
     if (group[i] < 0 || group[i] > 2 || stream[i] < 0 || stream[i] >= n_streams) return -1;
     auto lk = tg.acquire(static_cast<hkv::Group>(group[i]), stream[i]);
