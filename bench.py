@@ -56,7 +56,7 @@ def parse_args(argv=None):
     p.add_argument("--batch", type=int, default=BATCH)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--e2e-depth", type=int, default=8, help="staging slots of the e2e pipeline")
+    p.add_argument("--e2e-depth", type=int, default=6, help="staging slots of the e2e pipeline")
     p.add_argument("--l2-residency", action="store_true",
                    help="keep each table's digest array persisting in L2 (hkv_set_l2_residency)")
     p.add_argument("--no-random-access", action="store_true",
