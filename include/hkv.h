@@ -277,9 +277,9 @@ enum {
   HKV_CNT_TIMEOUT_FREE = 15,   /* free-slot claims that ran out of attempts */
   HKV_CNT_TIMEOUT_EVICT = 16,  /* victim searches that ran out of attempts */
   HKV_CNT_TIMEOUT_WHY = 17,    /* last such search's last failure: 1 a locked
-                                  candidate, 2 no candidate, 3 lost the CAS,
-                                  4 score changed under the lock, 5 lost a
-                                  free-slot CAS */
+                                  candidate, 2 no candidate, 3 lost the
+                                  (key, score) CAS, 5 lost a free-slot
+                                  CAS */
   HKV_CNT_TIMEOUT_KEY = 18,    /* its key */
   HKV_CNT_UPD_CLAIMS = 19,     /* free-slot claims made by the update phase
                                   (included in HKV_CNT_INSERTED) */

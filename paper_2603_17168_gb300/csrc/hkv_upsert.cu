@@ -29,11 +29,11 @@
 // Single-bucket claims are linearisable: while a bucket is full a slot's
 // (score, key) only grows; a victim search that meets a locked slot among
 // the minimum-score candidates re-reads instead of choosing around it; and
-// the victim's score is re-checked under its lock, which catches a score
-// and key read from two different occupants. Any serial order of "insert if
-// free, else replace the minimum iff larger" ends with each bucket holding
-// the largest 128 (score, key) pairs, so the single-bucket result does not
-// depend on the schedule.
+// the victim is locked with one 128-bit CAS on its (key, score) pair, which
+// fails for a key and score read from two different occupants. Any serial
+// order of "insert if free, else replace the minimum iff larger" ends with
+// each bucket holding the largest 128 (score, key) pairs, so the
+// single-bucket result does not depend on the schedule.
 #include "hkv_internal.h"
 
 namespace hkv {
@@ -209,6 +209,24 @@ __global__ void __launch_bounds__(kDedupThreads)
 // other lanes' value stores), becomes visible before the key does.
 __device__ __forceinline__ void publish_key(uint64_t* addr, uint64_t key) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(addr), "l"(key) : "memory");
+}
+
+// Compare-and-swap of a slot's whole (key, score) pair with one 128-bit
+// atomic (sm_90 and later): succeeds iff the pair still equals
+// (key_old, score_old), which then becomes (key_new, score_new).
+__device__ __forceinline__ bool cas_pair(uint64_t* pair, uint64_t key_old, uint64_t score_old,
+                                         uint64_t key_new, uint64_t score_new) {
+  unsigned long long k, sc;
+  asm volatile(
+      "{\n\t.reg .b128 cmp, swp, old;\n\t"
+      "mov.b128 cmp, {%2, %3};\n\t"
+      "mov.b128 swp, {%4, %5};\n\t"
+      "atom.relaxed.gpu.global.cas.b128 old, [%6], cmp, swp;\n\t"
+      "mov.b128 {%0, %1}, old;\n\t}"
+      : "=l"(k), "=l"(sc)
+      : "l"(key_old), "l"(score_old), "l"(key_new), "l"(score_new), "l"(pair)
+      : "memory");
+  return k == key_old && sc == score_old;
 }
 
 // L2 prefetch of a contiguous range with one TMA bulk instruction
@@ -670,25 +688,20 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
         }
         const unsigned own = __ballot_sync(kFull, qbest >= 0 && mine);
         const int owner = __ffs(own) - 1;
-        int ok = 0, stale = 0;
+        int ok = 0;
         uint64_t g = 0;
         if (lane == owner) {
           const uint64_t bqk = qbest < 4 ? b1 : b2;
           g = bqk * kSlots + (uint64_t)held_slot(lane, qbest & 3);
-          ok = atomicCAS(reinterpret_cast<unsigned long long*>(key_ptr(t, g)), kmin,
-                         kLockedKey) == kmin;
-          // A score and key read from two different occupants of the slot
-          // would show here as a changed score: release and start over.
-          if (ok && __ldcg(reinterpret_cast<const unsigned long long*>(score_ptr(t, g))) != smin) {
-            atomicExch(reinterpret_cast<unsigned long long*>(key_ptr(t, g)), kmin);
-            ok = 0;
-            stale = 1;
-          }
+          // Lock the victim only if its pair is still the (key, score) the
+          // minimum was read from: a key and score read from two different
+          // occupants of the slot cannot pass.
+          ok = cas_pair(key_ptr(t, g), kmin, smin, kLockedKey, smin);
         }
         ok = __shfl_sync(kFull, ok, owner);
         g = __shfl_sync(kFull, g, owner);
         if (!ok) {
-          why = __shfl_sync(kFull, stale, owner) ? 4u : 3u;
+          why = 3u;
           retries += lane == 0;
           continue;
         }
