@@ -48,7 +48,15 @@ struct DedupEntry {
 };
 static_assert(sizeof(DedupEntry) == 16, "dedup entry layout");
 
-enum : int { kCntUnique = 0, kCntEvOut = 1, kAbort = 2, kCntPending = 3, kCntWords = 8 };
+enum : int {
+  kCntUnique = 0,
+  kCntEvOut = 1,
+  kAbort = 2,
+  kCntPending = 3,
+  kCntInsCursor = 4,  // next 32-key chunk of phase I to hand out
+  kCntDeferred = 5,   // keys phase U left to phase I (mflag != 0)
+  kCntWords = 8
+};
 
 struct Scratch {
   DedupEntry* tab;
@@ -400,6 +408,7 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
   const uint64_t nwarps = ((uint64_t)gridDim.x * kUpdThreads) >> 5;
   const uint64_t nu = s.cnt[kCntUnique];
   unsigned updated = 0, lines = 0, kreads = 0, inserted = 0, ins_lines = 0, retries = 0;
+  unsigned deferred = 0;
 
   for (uint64_t base = warp * KPW; base < nu; base += nwarps * KPW) {
     const uint64_t u = base + (lane / G);
@@ -469,6 +478,7 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
         if (flag) {
           s.mi[u] = (uint32_t)i;
           s.mm[u] = (uint32_t)m;
+          deferred++;
         }
       }
     }
@@ -477,6 +487,7 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
                         HKV_CNT_UPD_CLAIMS, HKV_CNT_UPD_CLAIM_LINES, HKV_CNT_RETRIES};
   const unsigned vals[7] = {updated, lines, kreads, inserted, inserted, ins_lines, retries};
   flush_counts(t, which, vals);
+  if (UPSERT) block_reserve(s.cnt + kCntDeferred, deferred);
 }
 
 // --------------------------------------------------------- phase I insert
@@ -556,14 +567,26 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
     ctx.epoch = s.d->epoch;
   }
   const int lane = threadIdx.x & 31;
-  const uint64_t warp = (blockIdx.x * (uint64_t)kInsThreads + threadIdx.x) >> 5;
-  const uint64_t nwarps = ((uint64_t)gridDim.x * kInsThreads) >> 5;
   const uint64_t nu = s.cnt[kCntUnique];
   const uint64_t nchunks = (nu + 31) / 32;
   unsigned inserted = 0, evicted = 0, rejected = 0, retries = 0;
   unsigned score_lines = 0;
 
-  for (uint64_t c = warp; c < nchunks; c += nwarps) {
+  // Chunks of 32 distinct keys. With victim searches to do (at least one
+  // full-bucket key per chunk on average) a chunk goes to whichever warp
+  // is free next: how many searches a chunk holds varies widely, and a
+  // fixed stride left warps idle while others still searched. Otherwise a
+  // fixed stride, which spares the shared counter a burst of atomics.
+  const uint64_t warp = (blockIdx.x * (uint64_t)kInsThreads + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * kInsThreads) >> 5;
+  const bool dynamic = s.cnt[kCntDeferred] >= nchunks;
+  for (uint64_t k = 0;; ++k) {
+    unsigned long long c = warp + k * nwarps;
+    if (dynamic) {
+      if (lane == 0) c = atomicAdd(s.cnt + kCntInsCursor, 1ull);
+      c = __shfl_sync(kFull, c, 0);
+    }
+    if (c >= nchunks) break;
     // The chunk's 32 distinct keys: flags and miss records, coalesced.
     const uint64_t my_u = c * 32 + lane;
     const uint8_t my_flag = my_u < nu ? s.mflag[my_u] : 0;
