@@ -95,19 +95,33 @@ __device__ __forceinline__ void abort_batch(const Scratch& s, uint32_t* err, uin
 
 // ------------------------------------------------------------------- dedup
 
+// A tile of 1024 keys per block, deduplicated in a shared table of 1536
+// entries (load at most 2/3; 24 KiB), so that seven blocks fit an SM and a
+// batch of 2^20 keys (1024 blocks) runs in one wave on 152 SMs: blocks
+// spend most of their life waiting on global atomics, and a second wave
+// costs a whole block lifetime more.
 constexpr int kDedupThreads = 256;
 constexpr int kDedupKPT = 4;
 constexpr int kDedupTile = kDedupThreads * kDedupKPT;           // 1024 keys
-constexpr int kDedupSmemBits = 11;                              // 2048 entries
-constexpr int kDedupEntries = 1 << kDedupSmemBits;
-constexpr int kDedupPerThread = kDedupEntries / kDedupThreads;  // 8
+constexpr int kDedupEntries = 1536;
+constexpr int kDedupPerThread = kDedupEntries / kDedupThreads;  // 6
 constexpr int kDedupSmem = kDedupEntries * (int)sizeof(DedupEntry);
+constexpr int kDedupBlocksPerSm = 7;
+constexpr int kDedupMergeGroup = 3;  // global-table attempts a thread has in flight
+static_assert(kDedupEntries % kDedupThreads == 0 && kDedupPerThread % kDedupMergeGroup == 0,
+              "dedup table split");
+static_assert(2 * kDedupEntries >= 3 * kDedupTile, "dedup table load");
 
-__global__ void __launch_bounds__(kDedupThreads)
+// Home slot of a key in the shared table: the top 32 bits of the key's hash
+// scaled to [0, kDedupEntries).
+__device__ __forceinline__ uint32_t dedup_smem_pos(uint64_t key) {
+  return (uint32_t)((dedup_pos(key, 32) * (uint64_t)kDedupEntries) >> 32);
+}
+
+__global__ void __launch_bounds__(kDedupThreads, kDedupBlocksPerSm)
     dedup_kernel(uint64_t n, const uint64_t* __restrict__ keys, Scratch s, TableDev t,
                  int deterministic) {
   extern __shared__ DedupEntry sm[];
-  constexpr uint32_t kMask = kDedupEntries - 1;
   int tab_bits = s.tab_bits;
   uint64_t tab_mask = s.tab_mask;
   if (s.d) {  // grid sized for the batch object's largest round
@@ -141,11 +155,11 @@ __global__ void __launch_bounds__(kDedupThreads)
       abort_batch(s, t.err, HKV_ERR_RESERVED_KEY);
       continue;
     }
-    uint32_t p = (uint32_t)dedup_pos(k, kDedupSmemBits);
-    for (;;) {  // at most 1024 distinct keys in 2048 entries: terminates
+    uint32_t p = dedup_smem_pos(k);
+    for (;;) {  // at most 1024 distinct keys in 1536 entries: terminates
       const unsigned long long old = atomicCAS(&sm[p].key, kEmptyKey, (unsigned long long)k);
       if (old == kEmptyKey || old == k) break;
-      p = (p + 1) & kMask;
+      p = p + 1 == (uint32_t)kDedupEntries ? 0u : p + 1;
     }
     atomicMin(&sm[p].nlast, ~(uint32_t)idx);
     atomicAdd(&sm[p].cnt_m1, 1u);
@@ -153,22 +167,22 @@ __global__ void __launch_bounds__(kDedupThreads)
   }
   __syncthreads();
   // Merge this tile's distinct keys into the global table. A thread's
-  // entries go four at a time: their first CAS attempts are issued together
+  // entries go kDedupMergeGroup at a time: their first CAS attempts are issued together
   // (independent addresses), and only collisions walk on one by one.
   uint32_t gps[kDedupPerThread];
   unsigned nfirst = 0, firsts = 0;
 #pragma unroll
-  for (int h = 0; h < kDedupPerThread; h += 4) {
-    unsigned long long kq[4], old[4];
-    uint64_t gq[4];
+  for (int h = 0; h < kDedupPerThread; h += kDedupMergeGroup) {
+    unsigned long long kq[kDedupMergeGroup], old[kDedupMergeGroup];
+    uint64_t gq[kDedupMergeGroup];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < kDedupMergeGroup; ++j) {
       kq[j] = sm[threadIdx.x + (h + j) * kDedupThreads].key;
       gq[j] = dedup_pos(kq[j], tab_bits);
       old[j] = kq[j] != kEmptyKey ? atomicCAS(&s.tab[gq[j]].key, kEmptyKey, kq[j]) : 0ull;
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < kDedupMergeGroup; ++j) {
       const int q = h + j;
       const int p = threadIdx.x + q * kDedupThreads;
       gps[q] = 0;
