@@ -107,10 +107,35 @@ constexpr int kDedupEntries = 1536;
 constexpr int kDedupPerThread = kDedupEntries / kDedupThreads;  // 6
 constexpr int kDedupSmem = kDedupEntries * (int)sizeof(DedupEntry);
 constexpr int kDedupBlocksPerSm = 7;
-constexpr int kDedupMergeGroup = 3;  // global-table attempts a thread has in flight
-static_assert(kDedupEntries % kDedupThreads == 0 && kDedupPerThread % kDedupMergeGroup == 0,
-              "dedup table split");
+constexpr int kDedupMergeGroup = 2;  // global-table attempts a thread has in flight
+static_assert(kDedupTile / kDedupThreads <= 32, "dedup first-key mask");
+static_assert(kDedupEntries % kDedupThreads == 0, "dedup table split");
 static_assert(2 * kDedupEntries >= 3 * kDedupTile, "dedup table load");
+
+// Exclusive prefix sum of count over the block's threads (kDedupThreads);
+// *total receives the block's sum. Synchronises the block.
+__device__ __forceinline__ unsigned block_scan_excl(unsigned count, unsigned* total) {
+  constexpr int kWarps = kDedupThreads / 32;
+  __shared__ unsigned wsum[kWarps];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned incl = count;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  unsigned before = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const unsigned c = wsum[w];
+    before += w < wid ? c : 0u;
+    tot += c;
+  }
+  *total = tot;
+  return before + incl - count;
+}
 
 // Home slot of a key in the shared table: the top 32 bits of the key's hash
 // scaled to [0, kDedupEntries).
@@ -166,41 +191,63 @@ __global__ void __launch_bounds__(kDedupThreads, kDedupBlocksPerSm)
     pos[j] = (int)p;
   }
   __syncthreads();
-  // Merge this tile's distinct keys into the global table. A thread's
-  // entries go kDedupMergeGroup at a time: their first CAS attempts are issued together
-  // (independent addresses), and only collisions walk on one by one.
-  uint32_t gps[kDedupPerThread];
-  unsigned nfirst = 0, firsts = 0;
+  // The occupied entries (one per distinct key of the tile, so at most
+  // kDedupTile) as a dense list, so that each thread merges at most
+  // kDedupMergeGroup of them per round of global round trips.
+  __shared__ uint16_t occ[kDedupTile];
+  unsigned mine = 0;
 #pragma unroll
-  for (int h = 0; h < kDedupPerThread; h += kDedupMergeGroup) {
+  for (int q = 0; q < kDedupPerThread; ++q)
+    mine += sm[threadIdx.x + q * kDedupThreads].key != kEmptyKey ? 1u : 0u;
+  unsigned nocc;
+  unsigned o = block_scan_excl(mine, &nocc);
+#pragma unroll
+  for (int q = 0; q < kDedupPerThread; ++q) {
+    const int p = threadIdx.x + q * kDedupThreads;
+    if (sm[p].key != kEmptyKey) occ[o++] = (uint16_t)p;
+  }
+  __syncthreads();
+  // Merge the listed keys into the global table. A thread's keys of a round
+  // go together: their CAS attempts are issued at once (independent
+  // addresses), and keys that met another key walk on in lockstep, one
+  // round trip per step for all of them.
+  unsigned nfirst = 0, firsts = 0;  // bit m: list item threadIdx.x + m * kDedupThreads
+  for (unsigned r0 = 0; r0 < nocc; r0 += kDedupMergeGroup * kDedupThreads) {
     unsigned long long kq[kDedupMergeGroup], old[kDedupMergeGroup];
     uint64_t gq[kDedupMergeGroup];
+    int pp[kDedupMergeGroup];
 #pragma unroll
     for (int j = 0; j < kDedupMergeGroup; ++j) {
-      kq[j] = sm[threadIdx.x + (h + j) * kDedupThreads].key;
+      const unsigned r = r0 + j * kDedupThreads + threadIdx.x;
+      pp[j] = r < nocc ? (int)occ[r] : -1;
+      kq[j] = pp[j] >= 0 ? sm[pp[j]].key : kEmptyKey;
       gq[j] = dedup_pos(kq[j], tab_bits);
-      old[j] = kq[j] != kEmptyKey ? atomicCAS(&s.tab[gq[j]].key, kEmptyKey, kq[j]) : 0ull;
+      old[j] = kq[j] != kEmptyKey ? atomicCAS(&s.tab[gq[j]].key, kEmptyKey, kq[j]) : kEmptyKey;
+    }
+    // the table holds >= 2n entries: every walk ends
+    for (;;) {
+      bool walking = false;
+#pragma unroll
+      for (int j = 0; j < kDedupMergeGroup; ++j)
+        if (old[j] != kEmptyKey && old[j] != kq[j]) {
+          gq[j] = (gq[j] + 1) & tab_mask;
+          old[j] = atomicCAS(&s.tab[gq[j]].key, kEmptyKey, kq[j]);
+          walking = true;
+        }
+      if (!walking) break;
     }
 #pragma unroll
     for (int j = 0; j < kDedupMergeGroup; ++j) {
-      const int q = h + j;
-      const int p = threadIdx.x + q * kDedupThreads;
-      gps[q] = 0;
-      if (kq[j] == kEmptyKey) continue;
-      // the table holds >= 2n entries: terminates
-      while (old[j] != kEmptyKey && old[j] != kq[j]) {
-        gq[j] = (gq[j] + 1) & tab_mask;
-        old[j] = atomicCAS(&s.tab[gq[j]].key, kEmptyKey, kq[j]);
-      }
+      if (pp[j] < 0) continue;
+      const int p = pp[j];
       const bool first = old[j] == kEmptyKey;
       const uint32_t c = sm[p].cnt_m1 + 1u;
       atomicMin(&s.tab[gq[j]].nlast, sm[p].nlast);
       atomicAdd(&s.tab[gq[j]].cnt_m1, c);
       if (deterministic && (!first || c > 1)) abort_batch(s, t.err, HKV_ERR_DUPLICATE_KEY);
-      gps[q] = (uint32_t)gq[j];
       sm[p].cnt_m1 = (uint32_t)gq[j];  // reuse: global entry of this key
       if (first) {
-        firsts |= 1u << q;
+        firsts |= 1u << (r0 / kDedupThreads + j);
         nfirst++;
       }
     }
@@ -208,11 +255,11 @@ __global__ void __launch_bounds__(kDedupThreads, kDedupBlocksPerSm)
   // One list reservation per block for the keys this block saw first
   // (block_reserve also synchronises the block: the smem entries are final).
   unsigned long long u = block_reserve(s.cnt + kCntUnique, nfirst);
-#pragma unroll
-  for (int q = 0; q < kDedupPerThread; ++q)
-    if (firsts & (1u << q)) {
-      s.ulist[u] = gps[q];
-      s.mkey[u] = sm[threadIdx.x + q * kDedupThreads].key;
+  for (int m = 0; m < kDedupTile / kDedupThreads; ++m)
+    if (firsts & (1u << m)) {
+      const int p = occ[threadIdx.x + m * kDedupThreads];
+      s.ulist[u] = sm[p].cnt_m1;
+      s.mkey[u] = sm[p].key;
       ++u;
     }
 #pragma unroll
