@@ -988,7 +988,14 @@ __global__ void __launch_bounds__(kOrdThreads)
 // --------------------------------------------------------------- reconcile
 
 constexpr int kRecThreads = 256;
+constexpr int kRecPerThread = 4;  // distinct keys a thread has in flight per round
 
+// Every distinct key whose phase I displaced a resident entry reports that
+// entry as evicted, unless the displaced key is itself a key of this batch
+// inserted earlier in the same call (then it is refused instead). A round
+// takes kRecPerThread keys per thread, strided by the grid: their loads and
+// dedup-chain walks are in flight together, and one list reservation per
+// block covers all of them.
 __global__ void __launch_bounds__(kRecThreads)
     reconcile_kernel(TableDev t, Scratch s, uint64_t* __restrict__ ev_keys,
                      uint64_t* __restrict__ ev_scores, float* __restrict__ ev_values) {
@@ -996,37 +1003,69 @@ __global__ void __launch_bounds__(kRecThreads)
   const int tab_bits = s.d ? tab_bits_for(s.d->n) : s.tab_bits;
   const uint64_t tab_mask = (1ull << tab_bits) - 1;
   const uint64_t nu = s.cnt[kCntUnique];
+  const uint64_t stride = (uint64_t)gridDim.x * kRecThreads;
   for (uint64_t base = (uint64_t)blockIdx.x * kRecThreads; base < nu;
-       base += (uint64_t)gridDim.x * kRecThreads) {
-    const uint64_t u = base + threadIdx.x;
-    uint64_t k = kEmptyKey;
-    if (u < nu && s.mflag[u]) k = s.evk[u];
-    bool out = k != kEmptyKey;
-    if (out) {
-      uint64_t gp = dedup_pos(k, tab_bits);
-      for (;;) {
-        const uint64_t tk = s.tab[gp].key;
-        if (tk == k) {
-          // displaced by a later key of this batch: not an eviction
-          if (s.tstatus[gp] == HKV_ST_INSERTED) {
-            s.tstatus[gp] = HKV_ST_REJECTED;
-            out = false;
-          }
-          break;
-        }
-        if (tk == kEmptyKey) break;
-        gp = (gp + 1) & tab_mask;
-      }
+       base += kRecPerThread * stride) {
+    uint64_t k[kRecPerThread], gp[kRecPerThread];
+    bool out[kRecPerThread], walking[kRecPerThread];
+    uint8_t f[kRecPerThread];
+#pragma unroll
+    for (int r = 0; r < kRecPerThread; ++r) {
+      const uint64_t u = base + r * stride + threadIdx.x;
+      f[r] = u < nu ? s.mflag[u] : 0;
     }
-    const unsigned long long o = block_reserve(s.cnt + kCntEvOut, out ? 1u : 0u);
-    if (out) {
-      if (ev_keys) ev_keys[o] = k;
+#pragma unroll
+    for (int r = 0; r < kRecPerThread; ++r) {
+      const uint64_t u = base + r * stride + threadIdx.x;
+      k[r] = f[r] ? s.evk[u] : kEmptyKey;
+    }
+#pragma unroll
+    for (int r = 0; r < kRecPerThread; ++r) {
+      out[r] = walking[r] = k[r] != kEmptyKey;
+      gp[r] = dedup_pos(k[r], tab_bits);
+    }
+    for (;;) {  // the table holds >= 2n entries: every walk ends
+      uint64_t tk[kRecPerThread];
+#pragma unroll
+      for (int r = 0; r < kRecPerThread; ++r) tk[r] = walking[r] ? s.tab[gp[r]].key : 0ull;
+      bool any = false;
+#pragma unroll
+      for (int r = 0; r < kRecPerThread; ++r) {
+        if (!walking[r]) continue;
+        if (tk[r] == k[r]) {
+          // displaced by a later key of this batch: not an eviction
+          if (s.tstatus[gp[r]] == HKV_ST_INSERTED) {
+            s.tstatus[gp[r]] = HKV_ST_REJECTED;
+            out[r] = false;
+          }
+          walking[r] = false;
+        } else if (tk[r] == kEmptyKey) {
+          walking[r] = false;
+        } else {
+          gp[r] = (gp[r] + 1) & tab_mask;
+          any = true;
+        }
+      }
+      if (!any) break;
+    }
+    unsigned cnt = 0;
+#pragma unroll
+    for (int r = 0; r < kRecPerThread; ++r) cnt += out[r] ? 1u : 0u;
+    unsigned long long o = block_reserve(s.cnt + kCntEvOut, cnt);
+#pragma unroll
+    for (int r = 0; r < kRecPerThread; ++r) {
+      if (!out[r]) continue;
+      const uint64_t u = base + r * stride + threadIdx.x;
+      if (ev_keys) ev_keys[o] = k[r];
       if (ev_scores) ev_scores[o] = s.evs[u];
       if (ev_values && s.evv)
         for (uint32_t d = 0; d < t.dim; ++d) ev_values[o * t.dim + d] = s.evv[u * t.dim + d];
+      ++o;
     }
   }
 }
+
+constexpr int kStatusPerThread = 4;  // positions a thread has in flight per round
 
 __global__ void status_kernel(uint64_t n, Scratch s, uint8_t* __restrict__ status_out,
                               uint64_t* __restrict__ n_evicted) {
@@ -1035,10 +1074,26 @@ __global__ void status_kernel(uint64_t n, Scratch s, uint8_t* __restrict__ statu
     n = s.d->n;
     status_out = s.d->flags;
   }
-  if (status_out)
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x)
-      status_out[i] = s.tstatus[s.slot_of[i]];
+  if (status_out) {
+    // each position's status is its dedup entry's: both loads of a round's
+    // positions go out together
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < n;
+         i0 += kStatusPerThread * stride) {
+      uint32_t e[kStatusPerThread];
+      uint8_t v[kStatusPerThread];
+#pragma unroll
+      for (int r = 0; r < kStatusPerThread; ++r) {
+        const uint64_t i = i0 + r * stride;
+        e[r] = i < n ? s.slot_of[i] : 0u;
+      }
+#pragma unroll
+      for (int r = 0; r < kStatusPerThread; ++r) v[r] = i0 + r * stride < n ? s.tstatus[e[r]] : 0;
+#pragma unroll
+      for (int r = 0; r < kStatusPerThread; ++r)
+        if (i0 + r * stride < n) status_out[i0 + r * stride] = v[r];
+    }
+  }
   if (n_evicted && blockIdx.x == 0 && threadIdx.x == 0) *n_evicted = s.cnt[kCntEvOut];
 }
 
@@ -1160,6 +1215,12 @@ unsigned grid_for(const hkv_table_s* t, uint64_t threads_needed, int block, int 
   return blocks ? (unsigned)blocks : 1u;
 }
 
+// Blocks of reconcile_kernel for a batch of n keys: kRecPerThread distinct
+// keys per thread, at most four blocks per SM (48 registers: all resident).
+unsigned reconcile_grid(const hkv_table_s* t, uint64_t n) {
+  return grid_for(t, (n + kRecPerThread - 1) / kRecPerThread, kRecThreads, 4);
+}
+
 template <int G, bool UPSERT>
 void launch_update_g(hkv_table_s* t, uint64_t n, const Scratch& s, const float* values,
                      const uint64_t* scores, ScoreCtx ctx, bool vec16, cudaStream_t st) {
@@ -1271,7 +1332,7 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
   }
   {
     KernelTimer timer(t->prof, HKV_K_RECONCILE, st);
-    reconcile_kernel<<<grid_for(t, n, kRecThreads, 8), kRecThreads, 0, st>>>(
+    reconcile_kernel<<<reconcile_grid(t, n), kRecThreads, 0, st>>>(
         t->dev, s, ev_keys, ev_scores, ev_values);
   }
   if (status_out || n_evicted) {
@@ -1394,7 +1455,7 @@ hkv_status launch_upsert_in(hkv_table_s* t, uint64_t n, const uint64_t* keys, co
   }
   {
     KernelTimer timer(t->prof, HKV_K_RECONCILE, st);
-    reconcile_kernel<<<grid_for(t, n, kRecThreads, 8), kRecThreads, 0, st>>>(
+    reconcile_kernel<<<reconcile_grid(t, n), kRecThreads, 0, st>>>(
         t->dev, s, ev_keys, ev_scores, nullptr);
   }
   if (status_out || n_evicted) {
@@ -1449,8 +1510,8 @@ hkv_status launch_upsert_desc(hkv_table_s* t, uint64_t n_max, const OpDesc* d, v
   else
     launch_table_kernel(t, insert_kernel<false>, ig, kInsThreads, 0, st, t->dev, s,
                         (const float*)nullptr, (const uint64_t*)nullptr, ScoreCtx{0, 0});
-  reconcile_kernel<<<grid_for(t, n, kRecThreads, 8), kRecThreads, 0, st>>>(t->dev, s, nullptr,
-                                                                             nullptr, nullptr);
+  reconcile_kernel<<<reconcile_grid(t, n), kRecThreads, 0, st>>>(t->dev, s, nullptr, nullptr,
+                                                                 nullptr);
   status_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(n, s, nullptr, nullptr);
   return cuda_status(cudaGetLastError(), "batched upsert launch");
 }
