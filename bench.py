@@ -41,9 +41,19 @@ UNIVERSE = 1 << 32
 ALPHA = 1.05
 NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6800.0
-WORKLOAD = ("single table x4 (lambda 0.50/0.75/0.90/1.00): 2^26 slots (2^19 buckets x 128), "
-            "dim 32 fp32, LFU, dual-bucket, uniform fill over 2^32, per step find + "
-            "insert_or_assign of 2^20 Zipf(1.05) keys per table")
+
+
+def single_workload(nb_log2=NB_LOG2, batch=BATCH, lambdas=LAMBDAS):
+    """Name of the single-table workload at the given sizes (the headline
+    configuration by default)."""
+    lam = "/".join(f"{x:.2f}" for x in lambdas)
+    n = f"2^{batch.bit_length() - 1}" if batch & (batch - 1) == 0 else str(batch)
+    return (f"single table x{len(lambdas)} (lambda {lam}): 2^{nb_log2 + 7} slots "
+            f"(2^{nb_log2} buckets x 128), dim {DIM} fp32, LFU, dual-bucket, uniform fill over "
+            f"2^32, per step find + insert_or_assign of {n} Zipf(1.05) keys per table")
+
+
+WORKLOAD = single_workload()
 
 
 def parse_args(argv=None):
@@ -518,16 +528,21 @@ def run_ours(args):
     result = None
     if rank == 0:
         value = units / (ms * 1e-3) / 1e9
+        # digests, (key, score) pairs and fp32 values per slot; per table and
+        # step the find's keys and rows out, the upsert's keys and rows in
+        table_gib = nb * 128 * (1 + 16 + 4 * DIM) / 2**30
+        step_gib = len(lambdas) * 2 * batch * (8 + 4 * DIM) / 2**30
         result = {
             "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
             "steps": steps, "warmup": warm, "ms_per_step": round(ms / steps, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic (seeded uniform fill + Zipf(1.05) request keys over 2^32, N(0,1) fp32 values)",
-            "config": {"workload": WORKLOAD, "buckets_per_table": nb, "slots_per_table": nb * 128,
+            "config": {"workload": single_workload(args.nb_log2, batch, lambdas),
+                       "buckets_per_table": nb, "slots_per_table": nb * 128,
                        "dim": DIM, "batch": batch, "policy": "LFU", "dual_bucket": True,
                        "lambdas": list(lambdas), "parallelism": f"replicas x{world}",
-                       "l2": "no flush: each table is 9.1 GiB and a step's inputs 1.1 GiB, "
-                             "both far above the 129 MB L2",
+                       "l2": f"no flush: each table is {table_gib:.1f} GiB and a step's "
+                             f"inputs {step_gib:.2f} GiB, both far above the 129 MB L2",
                        "launch": {"find_tpk": args.find_tpk or "default",
                                   "update_tpk": args.update_tpk or "default"},
                        "l2_residency_bytes": [t.l2_residency for t in tables]},
