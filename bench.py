@@ -564,7 +564,10 @@ def run_e2e(tables, fk, uk, uv, warm, steps, batch, world, dev, depth=3):
     """The same steps end to end through the library's host-buffer pipeline
     (hkv_pipeline_*): every step's keys and rows start in page-locked host
     memory and every result (find rows and flags, upsert statuses) ends
-    there; the copies of neighbouring operations overlap the kernels."""
+    there; the copies of neighbouring operations overlap the kernels. Keys,
+    find rows and flags and statuses cross the link whole; an upsert sends
+    the rows of its distinct keys only (gathered after dedup), so those
+    bytes come from the tables' own counters over the timed steps."""
     import torch
     import paper_2603_17168_gb300 as hkv
     pin = lambda x: x.cpu().pin_memory()  # noqa: E731
@@ -584,12 +587,15 @@ def run_e2e(tables, fk, uk, uv, warm, steps, batch, world, dev, depth=3):
             pipe.find(t, fk_h[i], ov_h[j], of_h[j])
             pipe.insert_or_assign(t, uk_h[i], uv_h[i], status=os_h[j])
             if count:
-                h2d += fk_h[i].numel() * 8 + uk_h[i].numel() * 8 + uv_h[i].numel() * 4
+                h2d += fk_h[i].numel() * 8 + uk_h[i].numel() * 8
                 d2h += ov_h[j].numel() * 4 + of_h[j].numel() + os_h[j].numel()
 
     for i in range(warm):
         step(i, False)
     pipe.sync()
+    for t in tables:
+        t.reset_counters()
+    torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
     for i in range(warm, warm + steps):
@@ -598,12 +604,14 @@ def run_e2e(tables, fk, uk, uv, warm, steps, batch, world, dev, depth=3):
     t1 = time.perf_counter()
     barrier(world)
     pipe.close()
+    for t in tables:
+        h2d += t.read_counters()["unique"] * DIM * 4
     ms, units = reduce_max_sum((t1 - t0) * 1e3, float(steps * len(tables) * 2 * batch), world, dev)
     return {"value": round(units / (ms * 1e-3) / 1e9, 4), "unit": UNIT,
             "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
             "ms_per_step": round(ms / steps, 4),
             "path": "hkv_pipeline_find / hkv_pipeline_insert_or_assign on page-locked host "
-                    f"buffers, {depth} staging slots"}
+                    f"buffers, {depth} staging slots; upsert rows of distinct keys only"}
 
 
 # -------------------------------------------------------------- the oracle

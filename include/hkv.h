@@ -411,8 +411,13 @@ hkv_status hkv_serve_destroy(hkv_server_t s);
  * cudaHostRegister) is needed for the copies to overlap, pageable memory
  * works but serialises them. Arguments: keys [n], values [n][dim] (find:
  * output, the rows of misses are zeros; upsert: input), found[n] /
- * status[n] (nullable), scores[n] (HKV_CUSTOM upserts, else NULL).
- * HKV_ERR_INVALID_ARG for n > max_keys, dim > max_dim or a null required
+ * status[n] (nullable), scores[n] (HKV_CUSTOM upserts, else NULL). An
+ * upsert whose `values` the device can address (page-locked host memory
+ * mapped into its address space, checked per call with
+ * cudaPointerGetAttributes on the first and last byte) sends only the rows
+ * the table can store: after dedup one kernel gathers the row of each
+ * distinct key's last occurrence into the slot, so rows of duplicates never
+ * cross the link; other host memory is copied whole. HKV_ERR_INVALID_ARG for n > max_keys, dim > max_dim or a null required
  * buffer; evictions are not reported. */
 typedef struct hkv_pipeline_s *hkv_pipeline_t;
 hkv_status hkv_pipeline_create(uint64_t max_keys, uint32_t max_dim, int depth,

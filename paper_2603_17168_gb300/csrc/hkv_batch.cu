@@ -174,6 +174,7 @@ hkv_status hkv_batch_run(hkv_batch_t b, const hkv_batch_op* ops, int use_graph,
     d.values_out = o.values_out;
     d.flags = o.flags;
     d.scores = t->opts.policy == HKV_CUSTOM ? o.scores : nullptr;
+    d.row_prefetch = o.op == HKV_OP_UPSERT && hkv::in_device_memory(o.values_in) ? 1 : 0;
     d.step = t->step;
     d.epoch = t->epoch;
     if (o.op == HKV_OP_UPSERT && o.n) d.step = ++t->step;

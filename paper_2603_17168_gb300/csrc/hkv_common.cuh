@@ -64,6 +64,7 @@ struct OpDesc {
   const uint64_t* scores;   // caller scores (HKV_CUSTOM), else null
   uint64_t step;
   uint64_t epoch;
+  int row_prefetch;         // values_in is device memory (bulk L2 prefetch allowed)
 };
 
 // log2 of the dedup table size for a batch of n keys (>= 2n, >= 1024).

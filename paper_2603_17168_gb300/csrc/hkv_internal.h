@@ -171,7 +171,18 @@ hkv_status launch_gather(const float* const* ptrs, uint64_t n, uint32_t dim, flo
 hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,
                          const uint64_t* scores, uint8_t* status_out, uint64_t* ev_keys,
                          uint64_t* ev_scores, float* ev_values, uint64_t* n_evicted,
-                         ScoreCtx ctx, cudaStream_t s, bool keep_hits = false);
+                         ScoreCtx ctx, cudaStream_t s, bool keep_hits = false,
+                         const float* gather_src = nullptr);
+// insert_or_assign whose rows sit in memory the kernels read slowly (mapped
+// page-locked host memory, `rows_src`): after dedup, the rows of the
+// batch's distinct keys (their last occurrences) are gathered into
+// `rows_stage` (device, n x dim) by one streaming kernel, and the update and
+// insert phases read them there. Results as hkv_insert_or_assign with
+// values = rows_src; evictions are not reported.
+hkv_status insert_or_assign_gathered(hkv_table_s* t, uint64_t n, const uint64_t* keys,
+                                     const float* rows_src, float* rows_stage,
+                                     const uint64_t* scores, uint8_t* status_out,
+                                     cudaStream_t s);
 // find_or_insert (Sec. 4.1): upsert that leaves residents' values alone,
 // then a find into values_io; found_out from the statuses.
 hkv_status launch_find_or_insert(hkv_table_s* t, uint64_t n, const uint64_t* keys,
@@ -187,6 +198,10 @@ hkv_status launch_upsert_in(hkv_table_s* t, uint64_t n, const uint64_t* keys, co
 // OpDesc; grids are sized for n_max, scratch is the caller's block of
 // upsert_scratch_bytes(n_max) bytes. No allocation, no profiling events.
 uint64_t upsert_scratch_bytes(uint64_t n_max);
+// True iff p points into device memory of the current device. Input rows
+// anywhere else (page-locked host memory that kernels read in place) get
+// plain loads only: no bulk L2 prefetch is issued on them.
+bool in_device_memory(const void* p);
 hkv_status launch_find_desc(hkv_table_s* t, uint64_t n_max, const OpDesc* d, bool values,
                             cudaStream_t s);
 hkv_status launch_upsert_desc(hkv_table_s* t, uint64_t n_max, const OpDesc* d, void* scratch,

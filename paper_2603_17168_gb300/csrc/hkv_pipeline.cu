@@ -5,18 +5,28 @@
 // queued as three stream-ordered pieces:
 //
 //   copy-in   stream: wait until the slot's previous results left the
-//             device, copy the inputs (keys, rows, scores) into the slot;
+//             device, copy the inputs (keys, scores; rows if staged) into
+//             the slot;
 //   compute   stream: wait for the copy-in, run hkv_find /
 //             hkv_insert_or_assign on the slot's buffers;
 //   copy-out  stream: wait for the compute, copy the results (rows and
 //             found flags, or statuses) to the caller's host buffers and
 //             mark the slot free.
 //
+// An upsert's rows are not copied whole: when the caller's buffer is memory
+// the device can address (page-locked host memory), one streaming kernel on
+// the compute stream gathers, right after dedup, only the rows the table
+// can store (the last occurrence of each distinct key) into the slot, and
+// the update and insert phases read them there. Duplicates' rows never
+// cross the link. Other host memory is staged whole by the copy engine.
+// A find's rows go back whole by the copy engine (kernels storing into host
+// memory beside the probe kernels took their block slots and lost).
+//
 // The compute stream runs operations in call order (they may share a
-// table), while the two copy engines work on the neighbouring operations:
-// with three slots, operation k's inputs arrive while operation k-1 computes
-// and operation k-2's results leave. Host-to-device and device-to-host copies
-// use the two directions of the link at once.
+// table), while the copy streams work on the neighbouring operations: with
+// three slots, operation k's inputs arrive while operation k-1 computes and
+// operation k-2's results leave. The two directions of the link are used at
+// once.
 #include <vector>
 
 #include "hkv_internal.h"
@@ -32,6 +42,32 @@ struct PipeSlot {
 };
 
 uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+// Device address of a host range [p, p + bytes) if every byte of it can be
+// read and written by kernels of the current device (page-locked host
+// memory mapped into its address space, or device or managed memory), else
+// null: then the range is reached by staging copies only.
+void* device_view(const void* p, uint64_t bytes) {
+  if (!p || bytes == 0) return nullptr;
+  const char* first = static_cast<const char*>(p);
+  const char* last = first + bytes - 1;
+  cudaPointerAttributes a{}, b{};
+  if (cudaPointerGetAttributes(&a, first) != cudaSuccess ||
+      cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  auto usable = [](const cudaPointerAttributes& x) {
+    return (x.type == cudaMemoryTypeHost || x.type == cudaMemoryTypeDevice ||
+            x.type == cudaMemoryTypeManaged) &&
+           x.devicePointer != nullptr;
+  };
+  if (!usable(a) || !usable(b)) return nullptr;
+  // one contiguous mapping from the first byte to the last
+  if (static_cast<char*>(b.devicePointer) != static_cast<char*>(a.devicePointer) + (bytes - 1))
+    return nullptr;
+  return a.devicePointer;
+}
 
 }  // namespace
 
@@ -158,16 +194,24 @@ hkv_status hkv_pipeline_insert_or_assign(hkv_pipeline_t p, hkv_table_t t, uint64
   if (n && (!keys || !values)) return bad_arg("pipeline upsert buffers");
   if (n && t->opts.policy == HKV_CUSTOM && !scores) return bad_arg("HKV_CUSTOM needs scores");
   if (n == 0) return HKV_OK;
+  const uint64_t row_bytes = n * t->opts.dim * 4ull;
+  // Rows the device can address are gathered after dedup (only the distinct
+  // keys' last occurrences); other rows are staged whole.
+  const float* rows_dev = static_cast<const float*>(device_view(values, row_bytes));
   PipeSlot& s = take_slot(p);
   cudaMemcpyAsync(s.keys, keys, n * 8, cudaMemcpyHostToDevice, p->in);
-  cudaMemcpyAsync(s.rows, values, n * t->opts.dim * 4ull, cudaMemcpyHostToDevice, p->in);
+  if (!rows_dev) cudaMemcpyAsync(s.rows, values, row_bytes, cudaMemcpyHostToDevice, p->in);
   const bool custom = t->opts.policy == HKV_CUSTOM;
   if (custom) cudaMemcpyAsync(s.scores, scores, n * 8, cudaMemcpyHostToDevice, p->in);
   cudaEventRecord(s.in_done, p->in);
   cudaStreamWaitEvent(p->compute, s.in_done, 0);
-  hkv_status rc = hkv_insert_or_assign(t, n, s.keys, s.rows, custom ? s.scores : nullptr,
-                                       status ? s.flags : nullptr, nullptr, nullptr, nullptr,
-                                       nullptr, p->compute);
+  hkv_status rc =
+      rows_dev ? hkv::insert_or_assign_gathered(t, n, s.keys, rows_dev, s.rows,
+                                                custom ? s.scores : nullptr,
+                                                status ? s.flags : nullptr, p->compute)
+               : hkv_insert_or_assign(t, n, s.keys, s.rows, custom ? s.scores : nullptr,
+                                      status ? s.flags : nullptr, nullptr, nullptr, nullptr,
+                                      nullptr, p->compute);
   cudaEventRecord(s.compute_done, p->compute);
   cudaStreamWaitEvent(p->out, s.compute_done, 0);
   if (status) cudaMemcpyAsync(status, s.flags, n, cudaMemcpyDeviceToHost, p->out);

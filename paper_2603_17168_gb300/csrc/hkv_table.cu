@@ -94,6 +94,15 @@ hkv_status fail(hkv_status s, const std::string& msg) {
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
+bool in_device_memory(const void* p) {
+  cudaPointerAttributes a{};
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice;
+}
+
 hkv_status cuda_status(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return HKV_OK;
   set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -573,3 +582,26 @@ hkv_status hkv_set_launch(hkv_table_t t, int find_tpk, int update_tpk) {
 }
 
 }  // extern "C"
+
+namespace hkv {
+
+hkv_status insert_or_assign_gathered(hkv_table_s* t, uint64_t n, const uint64_t* keys,
+                                     const float* rows_src, float* rows_stage,
+                                     const uint64_t* scores, uint8_t* status_out,
+                                     cudaStream_t s) {
+  if (!t || (n && (!keys || !rows_src || !rows_stage)))
+    return fail(HKV_ERR_INVALID_ARG, "upsert arguments");
+  if (n && t->opts.policy == HKV_CUSTOM && !scores)
+    return fail(HKV_ERR_INVALID_ARG, "HKV_CUSTOM needs scores");
+  if (n >= (1ull << 31)) return fail(HKV_ERR_INVALID_ARG, "batch above 2^31 keys");
+  auto lk = t->sched.acquire(kInserter, s);
+  ScoreCtx ctx{n ? t->step + 1 : t->step, t->epoch};
+  hkv_status rc = launch_upsert(t, n, keys, rows_stage,
+                                (t->opts.policy == HKV_CUSTOM) ? scores : nullptr, status_out,
+                                nullptr, nullptr, nullptr, nullptr, ctx, s, false, rows_src);
+  if (rc == HKV_OK && n) t->step++;
+  t->sched.release(s);
+  return rc;
+}
+
+}  // namespace hkv

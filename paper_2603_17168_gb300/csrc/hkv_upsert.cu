@@ -77,6 +77,8 @@ struct Scratch {
   unsigned long long* owner; // [B] ordered phase I: (wave, ~batch index) of
                              // each bucket's first pending key, or null
   int keep_hits;             // find_or_insert: residents keep their values
+  int row_prefetch;          // input rows are in device memory: the insert
+                             // phase may pull them into L2 by bulk prefetch
 };
 
 __device__ __forceinline__ uint64_t dedup_pos(uint64_t key, int bits) {
@@ -621,11 +623,13 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
     insert_kernel(TableDev t, Scratch s, const float* __restrict__ values,
                   const uint64_t* __restrict__ scores_in, ScoreCtx ctx) {
   if (aborted(s)) return;
+  int row_prefetch = s.row_prefetch;
   if (s.d) {
     values = s.d->values_in;
     scores_in = s.d->scores;
     ctx.step = s.d->step;
     ctx.epoch = s.d->epoch;
+    row_prefetch = s.d->row_prefetch;
   }
   const int lane = threadIdx.x & 31;
   const uint64_t nu = s.cnt[kCntUnique];
@@ -685,7 +689,8 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
         if (lane == l) {
           bulk_prefetch_l2(key_ptr(t, my_b1 * kSlots), kSlots * 16);
           if (my_two) bulk_prefetch_l2(key_ptr(t, my_b2 * kSlots), kSlots * 16);
-          if (VEC16) bulk_prefetch_l2(values + (uint64_t)my_i * t.dim, t.dim * 4);
+          if (VEC16 && row_prefetch)
+            bulk_prefetch_l2(values + (uint64_t)my_i * t.dim, t.dim * 4);
         }
       }
     }
@@ -701,7 +706,8 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
           if (lane == l) {
             bulk_prefetch_l2(key_ptr(t, my_b1 * kSlots), kSlots * 16);
             if (my_two) bulk_prefetch_l2(key_ptr(t, my_b2 * kSlots), kSlots * 16);
-            if (VEC16) bulk_prefetch_l2(values + (uint64_t)my_i * t.dim, t.dim * 4);
+            if (VEC16 && row_prefetch)
+              bulk_prefetch_l2(values + (uint64_t)my_i * t.dim, t.dim * 4);
           }
         }
       }
@@ -983,6 +989,35 @@ __global__ void __launch_bounds__(kOrdThreads)
   flush_counts(t, which, vals);
   const unsigned long long p = block_reserve(s.cnt + kCntPending, pending);
   (void)p;
+}
+
+// ------------------------------------------------- gather of input rows
+
+constexpr int kGatherThreads = 256;
+
+// For every distinct key of the batch, copy the row of its last occurrence
+// from src (rows the update and insert phases would read slowly in place,
+// e.g. page-locked host memory) to the same position of dst (device). One
+// thread per 16 bytes (vec16: dim % 4 == 0 and both arrays 16-byte aligned)
+// or per float; each pass of the grid has all of its loads in flight.
+__global__ void __launch_bounds__(kGatherThreads)
+    gather_last_rows_kernel(Scratch s, const float* __restrict__ src, float* __restrict__ dst,
+                            uint32_t dim, int vec16) {
+  if (aborted(s)) return;
+  const uint64_t nu = s.cnt[kCntUnique];
+  const uint32_t per_row = vec16 ? dim / 4 : dim;
+  const uint64_t units = nu * per_row;
+  for (uint64_t q = blockIdx.x * (uint64_t)kGatherThreads + threadIdx.x; q < units;
+       q += (uint64_t)gridDim.x * kGatherThreads) {
+    const uint64_t u = q / per_row;
+    const uint32_t j = (uint32_t)(q - u * per_row);
+    const uint64_t i = (uint32_t)~s.tab[s.ulist[u]].nlast;  // last occurrence of key u
+    if (vec16)
+      reinterpret_cast<float4*>(dst)[i * per_row + j] =
+          __ldg(reinterpret_cast<const float4*>(src) + i * per_row + j);
+    else
+      dst[i * dim + j] = __ldg(src + i * dim + j);
+  }
 }
 
 // --------------------------------------------------------------- reconcile
@@ -1301,7 +1336,7 @@ hkv_status run_ordered_phase_i(hkv_table_s* t, uint64_t n, const Scratch& s, con
 hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,
                          const uint64_t* scores, uint8_t* status_out, uint64_t* ev_keys,
                          uint64_t* ev_scores, float* ev_values, uint64_t* n_evicted,
-                         ScoreCtx ctx, cudaStream_t st, bool keep_hits) {
+                         ScoreCtx ctx, cudaStream_t st, bool keep_hits, const float* gather_src) {
   if (n == 0) {
     if (n_evicted) cudaMemsetAsync(n_evicted, 0, 8, st);
     return cuda_status(cudaGetLastError(), "upsert");
@@ -1310,9 +1345,17 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
   hkv_status rc = alloc_scratch(t, n, true, ev_values != nullptr, st, &a);
   if (rc) return rc;
   a.s.keep_hits = keep_hits ? 1 : 0;
+  a.s.row_prefetch = in_device_memory(values) ? 1 : 0;
   const Scratch& s = a.s;
-  const bool vec16 = t->dev.dim % 4 == 0 && aligned16(values);
+  const bool vec16 = t->dev.dim % 4 == 0 && aligned16(values) &&
+                     (gather_src == nullptr || aligned16(gather_src));
   launch_dedup(t, n, keys, s, st);
+  if (gather_src) {
+    // values is the staging array: fill the rows the later phases read
+    const uint64_t rows_max = n * (vec16 ? t->dev.dim / 4 : t->dev.dim);
+    gather_last_rows_kernel<<<grid_for(t, rows_max, kGatherThreads, 8), kGatherThreads, 0, st>>>(
+        s, gather_src, const_cast<float*>(values), t->dev.dim, vec16 ? 1 : 0);
+  }
   launch_update<true>(t, n, s, values, scores, ctx, vec16, st);
   if (s.owner) {
     rc = run_ordered_phase_i(t, n, s, values, scores, ctx, vec16, st);
@@ -1440,6 +1483,7 @@ hkv_status launch_upsert_in(hkv_table_s* t, uint64_t n, const uint64_t* keys, co
   // empty or zero.
   cudaMemsetAsync(s.tab, 0xFF, (s.tab_mask + 1) * sizeof(DedupEntry), st);
   cudaMemsetAsync(s.cnt, 0, kCntWords * 8, st);
+  s.row_prefetch = in_device_memory(values) ? 1 : 0;
   const bool vec16 = t->dev.dim % 4 == 0 && aligned16(values);
   launch_dedup(t, n, keys, s, st);
   launch_update<true>(t, n, s, values, scores, ctx, vec16, st);
