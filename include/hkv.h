@@ -153,7 +153,11 @@ hkv_status hkv_contains(hkv_table_t t, uint64_t n, const uint64_t *keys, uint8_t
  * their bucket (dual mode: of the less occupied candidate), or, when full,
  * replace the minimum-(score, key) entry if their (score, key) is larger
  * (dual mode: the minimum over both candidates), else are rejected.
- *   values     [n][dim], required.
+ *   values     [n][dim], required: device memory, or page-locked host memory
+ *              mapped into the device's address space (cudaHostAlloc /
+ *              cudaHostRegister), which the kernels then read in place
+ *              (slower: each stored row crosses the host link while the
+ *              kernels wait).
  *   scores     [n], required iff policy == HKV_CUSTOM, else ignored (NULL ok).
  *   status_out [n] HKV_ST_*, may be NULL.
  *   evicted_keys / evicted_scores / evicted_values ([n], [n], [n][dim]), may
@@ -214,7 +218,9 @@ hkv_status hkv_find_or_insert(hkv_table_t t, uint64_t n, const uint64_t *keys, f
 /* assign (updater; Sec. 3.5): for each resident key, overwrite its value
  * (last occurrence wins) and score per the policy; HKV_CUSTOM takes scores[]
  * when given, else keeps the old score. Missing keys are ignored; the bucket
- * structure never changes. values may be NULL (scores only). */
+ * structure never changes. values may be NULL (scores only); like the
+ * rows of hkv_insert_or_assign they may be device memory or mapped
+ * page-locked host memory. */
 hkv_status hkv_assign(hkv_table_t t, uint64_t n, const uint64_t *keys, const float *values,
                       const uint64_t *scores, hkv_stream_t stream);
 

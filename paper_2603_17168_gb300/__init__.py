@@ -150,12 +150,14 @@ def _u64_types():
     return (torch.uint64, torch.int64)
 
 
-def _need(t, dtype, shape, name):
+def _need(t, dtype, shape, name, pinned_ok=False):
     if t is None:
         return
     ok = t.dtype in dtype if isinstance(dtype, tuple) else t.dtype == dtype
-    if not (t.is_cuda and ok and t.is_contiguous()):
-        raise ValueError(f"{name}: needs a contiguous CUDA tensor of {dtype}")
+    where = t.is_cuda or (pinned_ok and t.is_pinned())
+    if not (where and ok and t.is_contiguous()):
+        kind = "CUDA or page-locked host" if pinned_ok else "CUDA"
+        raise ValueError(f"{name}: needs a contiguous {kind} tensor of {dtype}")
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
 
@@ -288,7 +290,8 @@ class Table:
         import torch
         n = keys.numel()
         _need(keys, _u64_types(), (n,), "keys")
-        _need(values, torch.float32, (n, self.dim), "values")
+        # rows may also be page-locked host memory, read in place by the kernels
+        _need(values, torch.float32, (n, self.dim), "values", pinned_ok=True)
         _need(scores, _u64_types(), (n,), "scores")
         _need(status_out, torch.uint8, (n,), "status_out")
         _need(evicted_keys, _u64_types(), None, "evicted_keys")
@@ -315,7 +318,8 @@ class Table:
         import torch
         n = keys.numel()
         _need(keys, _u64_types(), (n,), "keys")
-        _need(values, torch.float32, (n, self.dim), "values")
+        # rows may also be page-locked host memory, read in place by the kernels
+        _need(values, torch.float32, (n, self.dim), "values", pinned_ok=True)
         _need(scores, _u64_types(), (n,), "scores")
         _need(status_out, torch.uint8, (n,), "status_out")
         _need(evicted_keys, _u64_types(), None, "evicted_keys")
@@ -330,7 +334,8 @@ class Table:
         import torch
         n = keys.numel()
         _need(keys, _u64_types(), (n,), "keys")
-        _need(values, torch.float32, (n, self.dim), "values")
+        # rows may also be page-locked host memory, read in place by the kernels
+        _need(values, torch.float32, (n, self.dim), "values", pinned_ok=True)
         _need(scores, _u64_types(), (n,), "scores")
         _check(load_library().hkv_assign(self._h, n, _ptr(keys), _ptr(values), _ptr(scores),
                                          _stream(stream)))

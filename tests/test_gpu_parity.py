@@ -466,3 +466,42 @@ def test_find_or_insert_bit_exact(policy, dual, det):
         assert np.array_equal(host(found), ofound)
         assert np.array_equal(host(io).view(np.uint32), orows.view(np.uint32))
         same_state(export_state(t), o.export())
+
+
+def test_rows_from_page_locked_host_memory():
+    """insert_or_assign and assign read their rows in place from mapped
+    page-locked host memory: the same statuses, evicted sets and final state
+    as the same batches from device memory, through fills, updates and the
+    victim searches of full buckets (the key universe is 12x the capacity).
+    Single-bucket mode, whose results do not depend on the schedule; the row
+    paths are the same in dual mode."""
+    rng = np.random.default_rng(9300)
+    nb, dim = 32, 8
+    a = hkv.Table(nb * 128, dim, hkv.LFU)
+    b = hkv.Table(nb * 128, dim, hkv.LFU)
+    z = w.Zipf(0.9, 12 * nb * 128)
+    evicted = 0
+    for rnd in range(6):
+        n = 3000
+        keys = z.keys(rng, n)
+        vals = w.normal_values(rng, n, dim)
+        outs = []
+        for t, v in ((a, torch.from_numpy(vals.copy()).pin_memory()), (b, dev(vals))):
+            st = torch.empty(n, dtype=torch.uint8, device="cuda")
+            ek = torch.empty(n, dtype=torch.int64, device="cuda")
+            ne = torch.zeros(1, dtype=torch.int64, device="cuda")
+            t.insert_or_assign(dev(keys), v, None, st, ek, None, None, ne)
+            t.sync()
+            outs.append((host(st), np.sort(host(ek)[:int(ne.item())])))
+        assert np.array_equal(outs[0][0], outs[1][0]), "statuses"
+        assert np.array_equal(outs[0][1], outs[1][1]), "evicted keys"
+        evicted += outs[0][1].size
+        if rnd % 2:
+            ak = z.keys(rng, 500)
+            av = w.normal_values(rng, 500, dim)
+            a.assign(dev(ak), torch.from_numpy(av.copy()).pin_memory())
+            b.assign(dev(ak), dev(av))
+    a.sync()
+    b.sync()
+    assert evicted > 0, "no victim search ran"
+    same_state(export_state(a), export_state(b))
