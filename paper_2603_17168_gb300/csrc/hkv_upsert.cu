@@ -623,6 +623,8 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
     insert_kernel(TableDev t, Scratch s, const float* __restrict__ values,
                   const uint64_t* __restrict__ scores_in, ScoreCtx ctx) {
   if (aborted(s)) return;
+  // Phase U placed every key: no victim search (the same for the whole grid)
+  if (s.cnt[kCntDeferred] == 0) return;
   int row_prefetch = s.row_prefetch;
   if (s.d) {
     values = s.d->values_in;
@@ -1035,6 +1037,8 @@ __global__ void __launch_bounds__(kRecThreads)
     reconcile_kernel(TableDev t, Scratch s, uint64_t* __restrict__ ev_keys,
                      uint64_t* __restrict__ ev_scores, float* __restrict__ ev_values) {
   if (aborted(s)) return;
+  // Phase U placed every key, so no key displaced anything (grid-uniform)
+  if (s.cnt[kCntDeferred] == 0) return;
   const int tab_bits = s.d ? tab_bits_for(s.d->n) : s.tab_bits;
   const uint64_t tab_mask = (1ull << tab_bits) - 1;
   const uint64_t nu = s.cnt[kCntUnique];
