@@ -37,6 +37,12 @@ struct hkv_batch_s {
   cudaEvent_t ring_ev[kRing] = {};
   int ring = 0;
   std::map<std::vector<int>, cudaGraphExec_t> graphs;
+  // per slot: the last upsert row pointer and whether it is device memory
+  // (input rows get a bulk L2 prefetch only there); asked again only when
+  // the pointer changes, since a pointer query costs more host time than a
+  // round's other bookkeeping
+  std::vector<const float*> rows_seen;
+  std::vector<int> rows_on_device;
   std::mutex mu;
 };
 
@@ -106,6 +112,8 @@ hkv_status hkv_batch_create(int n_slots, const hkv_table_t* tables, const uint64
   for (int i = 0; i < n_slots && e == cudaSuccess; ++i) {
     b->tables.push_back(tables[i]);
     b->max_keys.push_back(max_keys[i]);
+    b->rows_seen.push_back(nullptr);
+    b->rows_on_device.push_back(0);
     const uint64_t bytes = hkv::upsert_scratch_bytes(max_keys[i]);
     void* p = nullptr;
     e = cudaMalloc(&p, bytes);
@@ -174,7 +182,11 @@ hkv_status hkv_batch_run(hkv_batch_t b, const hkv_batch_op* ops, int use_graph,
     d.values_out = o.values_out;
     d.flags = o.flags;
     d.scores = t->opts.policy == HKV_CUSTOM ? o.scores : nullptr;
-    d.row_prefetch = o.op == HKV_OP_UPSERT && hkv::in_device_memory(o.values_in) ? 1 : 0;
+    if (o.op == HKV_OP_UPSERT && o.values_in && o.values_in != b->rows_seen[i]) {
+      b->rows_seen[i] = o.values_in;
+      b->rows_on_device[i] = hkv::in_device_memory(o.values_in) ? 1 : 0;
+    }
+    d.row_prefetch = o.op == HKV_OP_UPSERT && o.values_in ? b->rows_on_device[i] : 0;
     d.step = t->step;
     d.epoch = t->epoch;
     if (o.op == HKV_OP_UPSERT && o.n) d.step = ++t->step;
