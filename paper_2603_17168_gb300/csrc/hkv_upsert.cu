@@ -98,20 +98,24 @@ __device__ __forceinline__ void abort_batch(const Scratch& s, uint32_t* err, uin
 // ------------------------------------------------------------------- dedup
 
 // A tile of 1024 keys per block, deduplicated in a shared table of 1536
-// entries (load at most 2/3; 24 KiB), so that seven blocks fit an SM and a
-// batch of 2^20 keys (1024 blocks) runs in one wave on 152 SMs: blocks
-// spend most of their life waiting on global atomics, and a second wave
-// costs a whole block lifetime more.
+// entries (load at most 2/3; 24 KiB). Blocks spend most of their life
+// waiting on global atomics, so a batch whose tiles do not all fit at once
+// pays a whole block lifetime for its second wave: batches of more than six
+// tiles per SM (2^20 keys: 1024 blocks on 152 SMs) take an instantiation
+// bounded to seven blocks per SM (32 registers), the others one bounded to
+// six (40 registers, no spills, faster per block).
 constexpr int kDedupThreads = 256;
 constexpr int kDedupKPT = 4;
 constexpr int kDedupTile = kDedupThreads * kDedupKPT;           // 1024 keys
 constexpr int kDedupEntries = 1536;
 constexpr int kDedupPerThread = kDedupEntries / kDedupThreads;  // 6
 constexpr int kDedupSmem = kDedupEntries * (int)sizeof(DedupEntry);
-constexpr int kDedupBlocksPerSm = 7;
 constexpr int kDedupMergeGroup = 2;  // global-table attempts a thread has in flight
 static_assert(kDedupTile / kDedupThreads <= 32, "dedup first-key mask");
 static_assert(kDedupEntries % kDedupThreads == 0, "dedup table split");
+// seven blocks' tables, static scratch (the entry list and scan words,
+// under 3 KiB) and per-block reserve fit an SM's 228 KiB
+static_assert(7 * (kDedupSmem + 3072 + 1024) <= 228 * 1024, "seven dedup blocks per SM");
 static_assert(2 * kDedupEntries >= 3 * kDedupTile, "dedup table load");
 
 // Exclusive prefix sum of count over the block's threads (kDedupThreads);
@@ -145,7 +149,8 @@ __device__ __forceinline__ uint32_t dedup_smem_pos(uint64_t key) {
   return (uint32_t)((dedup_pos(key, 32) * (uint64_t)kDedupEntries) >> 32);
 }
 
-__global__ void __launch_bounds__(kDedupThreads, kDedupBlocksPerSm)
+template <int MIN_BLOCKS>
+__global__ void __launch_bounds__(kDedupThreads, MIN_BLOCKS)
     dedup_kernel(uint64_t n, const uint64_t* __restrict__ keys, Scratch s, TableDev t,
                  int deterministic) {
   extern __shared__ DedupEntry sm[];
@@ -1291,12 +1296,14 @@ void launch_update(hkv_table_s* t, uint64_t n, const Scratch& s, const float* va
 
 void launch_dedup(hkv_table_s* t, uint64_t n, const uint64_t* keys, const Scratch& s,
                   cudaStream_t st) {
-  static const cudaError_t smem_ok = cudaFuncSetAttribute(
-      dedup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDedupSmem);
-  (void)smem_ok;
   const unsigned grid = (unsigned)((n + kDedupTile - 1) / kDedupTile);
   KernelTimer timer(t->prof, HKV_K_DEDUP, st);
-  dedup_kernel<<<grid, kDedupThreads, kDedupSmem, st>>>(n, keys, s, t->dev, t->opts.deterministic);
+  if (grid > (unsigned)t->num_sms * 6)
+    dedup_kernel<7><<<grid, kDedupThreads, kDedupSmem, st>>>(n, keys, s, t->dev,
+                                                             t->opts.deterministic);
+  else
+    dedup_kernel<6><<<grid, kDedupThreads, kDedupSmem, st>>>(n, keys, s, t->dev,
+                                                             t->opts.deterministic);
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
