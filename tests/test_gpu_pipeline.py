@@ -104,3 +104,41 @@ def test_pipeline_refuses_oversized_operations():
         hkv.Pipeline(100, 8, 1)  # depth below 2
     pipe.close()
     pipe2.close()
+
+
+def test_pipeline_deterministic_dual_bit_exact():
+    """Deterministic dual-bucket tables (ordered phase I) driven through the
+    pipeline from page-locked buffers, with the rows of each batch's keys
+    gathered after dedup, end in the same state, statuses and find results
+    as the same batches through the device-buffer calls, bit for bit."""
+    rng = np.random.default_rng(8200)
+    nb, dim = 16, 8
+    tp = hkv.Table(nb * 128, dim, hkv.LFU, dual_bucket=True, deterministic=True)
+    td = hkv.Table(nb * 128, dim, hkv.LFU, dual_bucket=True, deterministic=True)
+    pipe = hkv.Pipeline(3000, dim, 3)
+    universe = 6 * nb * 128
+    for rnd in range(6):
+        n = 1500 + 200 * rnd
+        keys = (rng.choice(universe, n, replace=False) + 1).astype(np.uint64)  # distinct
+        vals = w.normal_values(rng, n, dim)
+        sh = torch.empty(n, dtype=torch.uint8).pin_memory()
+        pipe.insert_or_assign(tp, _host(keys, True), _host(vals, True), status=sh)
+        sd = torch.empty(n, dtype=torch.uint8, device="cuda")
+        td.insert_or_assign(dev(keys), dev(vals), status_out=sd)
+        q = (rng.choice(universe, 1000, replace=False) + 1).astype(np.uint64)
+        vh = torch.full((1000, dim), -7.0).pin_memory()
+        fh = torch.empty(1000, dtype=torch.uint8).pin_memory()
+        pipe.find(tp, _host(q, True), vh, fh)
+        pipe.sync()
+        torch.cuda.synchronize()
+        assert np.array_equal(sh.numpy(), host(sd)), "statuses"
+        vd = torch.zeros((1000, dim), device="cuda")
+        fd = torch.empty(1000, dtype=torch.uint8, device="cuda")
+        td.find(dev(q), vd, fd)
+        torch.cuda.synchronize()
+        assert np.array_equal(fh.numpy(), host(fd))
+        assert np.array_equal(vh.numpy().view(np.uint32), host(vd).view(np.uint32))
+    tp.sync()
+    td.sync()
+    same_state(export_state(tp), export_state(td))
+    pipe.close()
