@@ -12,37 +12,28 @@
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds it (kNoAllocScratchBytes) until the process exits. Host code
 // cannot pass the array's name to a kernel (on the host that name is only a
-// stand-in symbol, not a device address), so the first call on each device
-// looks its device address up with cudaGetSymbolAddress, with that device
-// current, and caches it.
-#include <mutex>
-
+// stand-in symbol, not a device address), so every call looks its device
+// address up with cudaGetSymbolAddress, with the table's device current.
+// The address is not cached: a context torn down by cudaDeviceReset and
+// created again maps the array elsewhere, and a cached address would then
+// point at memory the new context does not own. The lookup costs far less
+// than the launches it precedes. The first lookup on a device may load the
+// library's device code there, which stream capture does not allow, so the
+// first call on each device must come before any capture.
 #include "hkv_internal.h"
 
 namespace {
 
 constexpr uint64_t kNoAllocScratchBytes = 5ull << 20;  // 5 MiB
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::mutex g_setup_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on `device` (which must be current).
-hkv_status scratch_address(int device, void** out) {
-  if (device < 0 || device >= kMaxDevices) {
-    hkv::set_last_error("device index out of range for the no-alloc scratch table");
-    return HKV_ERR_INVALID_ARG;
-  }
-  std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (!g_scratch_addr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return hkv::cuda_status(e, "no-alloc scratch address");
-    g_scratch_addr[device] = p;
-  }
-  *out = g_scratch_addr[device];
+// Device address of the scratch array in the current context.
+hkv_status scratch_address(void** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return hkv::cuda_status(e, "no-alloc scratch address");
+  *out = p;
   return HKV_OK;
 }
 
@@ -74,8 +65,13 @@ extern "C" hkv_status hkv_insert_or_assign_noalloc(hkv_table_t t, uint64_t n,
     hkv::set_last_error("make the table's device current before calling");
     return HKV_ERR_INVALID_ARG;
   }
+  if (t->opts.dual_bucket && t->opts.deterministic) {
+    hkv::set_last_error("hkv_insert_or_assign_noalloc: deterministic dual-bucket tables need "
+                        "the ordered waves of hkv_insert_or_assign");
+    return HKV_ERR_INVALID_ARG;
+  }
   void* scratch = nullptr;
-  hkv_status rc = scratch_address(device, &scratch);
+  hkv_status rc = scratch_address(&scratch);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   auto lk = t->sched.acquire(hkv::kInserter, s);

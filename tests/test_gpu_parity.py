@@ -174,6 +174,68 @@ def _current_values(o, keys):
     return v
 
 
+@pytest.mark.parametrize("det", [True, False])
+def test_dual_bucket_erase_and_reinsert(det):
+    """Erase on dual-bucket tables (Sec. 3.5, erase is an inserter) of keys
+    that sit in their second bucket as well as their first, then fresh keys
+    past lambda = 1, so that phase D1 of Algorithm 3 reads the occupancy the
+    erase lowered. Deterministic mode: statuses, evicted sets and the full
+    state including buckets equal the oracle's bit for bit after every call.
+    Concurrent mode: every invariant after every batch, exactly the resident
+    erased keys gone, the retained count within 0.1% of the oracle's, and
+    find on the GPU's state equal to the oracle loaded with it."""
+    rng = np.random.default_rng(9600 + det)
+    nb, dim = 1 << 10, 8
+    cap = nb * 128
+    t = hkv.Table(cap, dim, hkv.LFU, dual_bucket=True, deterministic=det)
+    o = oracle.OracleTable(nb, dim, oracle.LFU, True)
+
+    def upsert(keys):
+        vals = w.normal_values(rng, keys.size, dim)
+        if det:
+            compare_upsert(t, o, keys, vals, deterministic=True)
+            same_state(export_state(t), o.export())
+        else:
+            gst, gek, ges, _ = gpu_upsert(t, keys, vals)
+            o.insert_or_assign(keys, vals)
+            _check_batch_invariants(t, nb, keys, gst, gek, ges)
+
+    fill = w.uniform_keys(rng, int(0.985 * cap), distinct=True)
+    for chunk in np.array_split(fill, 5):
+        upsert(chunk)
+    gk, gs, gv, gb = export_state(t)
+    b1, b2, _ = oracle.map_keys(nb, True, gk)
+    second = gk[(gb == b2) & (b2 != b1)]
+    first = gk[gb == b1]
+    assert second.size > 500, second.size
+    er = np.concatenate([rng.choice(second, second.size // 2, replace=False),
+                         rng.choice(first, 3000, replace=False), w.uniform_keys(rng, 64)])
+    rng.shuffle(er)
+    before = gk.size
+    t.erase(dev(er))
+    o.erase(er)
+    t.sync()
+    gk2 = export_state(t)[0]
+    assert not np.any(np.isin(er, gk2)), "an erased key is still resident"
+    assert gk2.size == before - int(np.isin(er, gk).sum())
+    assert t.size() == gk2.size
+    if det:
+        same_state(export_state(t), o.export())
+    for _ in range(4):
+        upsert(w.uniform_keys(rng, cap // 6, distinct=True))
+    assert o.size() == cap
+    gs_, os_ = t.size(), o.size()
+    assert abs(gs_ - os_) <= 0.001 * os_, (gs_, os_)
+    q = np.concatenate([o.export()[0][:4000], er[:2000], w.uniform_keys(rng, 2000)])
+    if det:
+        compare_find(t, o, q)
+    else:
+        gk, gs, gv, gb = export_state(t)
+        ref = oracle.OracleTable(nb, dim, oracle.LFU, True)
+        ref.load(gk, gs, gv, gb)
+        compare_find(t, ref, np.concatenate([gk[:4000], er[:2000], w.uniform_keys(rng, 2000)]))
+
+
 def test_errors_leave_table_unchanged():
     rng = np.random.default_rng(1300)
     t = hkv.Table(16 * 128, 4, hkv.LRU, deterministic=True)

@@ -1,12 +1,15 @@
 """Serving loop (hkv_serve_run): a trace of find / upsert requests with
 Poisson arrivals, replayed through continuous batching and through the plain
-one-request-at-a-time path on two identical sets of tables. Every request's
-result is the same in the mix as alone (bit for bit: found masks, found
-values, statuses), the final table states agree, batching really merged
+one-request-at-a-time path on two identical sets of tables, and through the
+CPU oracle in arrival order (each table's requests as a FIFO: Algorithms 1-2
+per table, Sec. 3.2-3.3). Every request's result in the mix equals the
+oracle's (bit for bit: found masks, found values, statuses) and the result
+alone; the final table states equal the oracle's; batching really merged
 requests, and the HBM admission budget is enforced."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2603_17168_gb300 import workloads as w
 
 pytestmark = pytest.mark.gpu
@@ -22,16 +25,39 @@ DIMS = (8, 16, 32, 64)
 BUCKETS = (64, 32, 128, 16)
 
 
-def tables_filled(seed):
+def tables_filled(seed, use_oracle=False):
     rng = np.random.default_rng(seed)
     ts = []
     for b, d in zip(BUCKETS, DIMS):
-        t = hkv.Table(b * 128, d, hkv.LRU)
         k = w.uniform_keys(rng, b * 100, universe=60000)
-        t.insert_or_assign(dev(k), dev(w.normal_values(rng, k.size, d)))
+        v = w.normal_values(rng, k.size, d)
+        if use_oracle:
+            t = oracle.OracleTable(b, d, oracle.LRU)
+            t.insert_or_assign(k, v)
+        else:
+            t = hkv.Table(b * 128, d, hkv.LRU)
+            t.insert_or_assign(dev(k), dev(v))
         ts.append(t)
-    torch.cuda.synchronize()
+    if not use_oracle:
+        torch.cuda.synchronize()
     return ts
+
+
+def oracle_replay(items, seed):
+    """Each request's (found or status, rows) from the oracle, in arrival
+    order, on oracle tables filled like tables_filled(seed)."""
+    orc = tables_filled(seed, use_oracle=True)
+    out = []
+    for it in items:
+        o = orc[it["table"]]
+        keys = it["keys"].numpy().view(np.uint64)
+        if it["op"] == hkv.OP_FIND:
+            rows, found, _ = o.find(keys)
+            out.append((found.astype(np.uint8), rows))
+        else:
+            st, _, _, _ = o.insert_or_assign(keys, it["values"].numpy())
+            out.append((st, None))
+    return orc, out
 
 
 def trace(rng, n_req, rate):
@@ -74,17 +100,27 @@ def test_each_request_is_the_same_alone_and_in_the_mix():
     items_alone = clone_outputs(items)
     res_mix = s_mix.run(hkv.make_requests(items), batched=True, use_graph=True)
     res_alone = s_alone.run(hkv.make_requests(items_alone), batched=False)
-    for a, b in zip(items, items_alone):
+    orc, expect = oracle_replay(items, 9101)
+    n_hits = 0
+    for i, (a, b, (of, orows)) in enumerate(zip(items, items_alone, expect)):
         fa, fb = a["flags"].numpy(), b["flags"].numpy()
+        assert np.array_equal(fa, of), f"request {i}: flags differ from the oracle"
         assert np.array_equal(fa, fb)
         if a["op"] == hkv.OP_FIND:
             m = fa.astype(bool)
+            n_hits += int(m.sum())
+            assert np.array_equal(a["values"].numpy()[m].view(np.uint32),
+                                  orows[m].view(np.uint32)), f"request {i}: rows differ"
             assert np.array_equal(a["values"].numpy()[m].view(np.uint32),
                                   b["values"].numpy()[m].view(np.uint32))
         else:
             assert np.all(fa > 0)
-    for x, y in zip(mixed, alone):
-        same_state(export_state(x), export_state(y))
+    assert n_hits > 0
+    for x, y, o in zip(mixed, alone, orc):
+        same_state(export_state(x), o.export())
+        same_state(export_state(y), o.export())
+        assert x.get_step() == o.step
+        o.close()
     rounds_mix = len({r.round for r in res_mix})
     rounds_alone = len({r.round for r in res_alone})
     assert rounds_alone == len(items)

@@ -90,3 +90,59 @@ def test_noalloc_refuses_batches_above_its_limit():
     assert rc == 1
     assert b"HKV_NOALLOC_MAX_KEYS" in lib.hkv_last_error()
     assert t.size() == 0
+
+
+def test_noalloc_dual_bucket_keeps_the_invariants_and_the_pooled_count():
+    """Dual-bucket tables (the single-table benchmark's mode) under the
+    no-alloc call: concurrent phase D1 is order-dependent, so the check is
+    every structural invariant after each of two calls in a row, and a
+    retained count within 0.1% of the pooled call's on a twin table."""
+    import oracle
+    from tests import invariants as inv
+
+    lib = hkv.load_library()
+    rng = np.random.default_rng(4300)
+    nb, dim = 256, 8
+    pooled = hkv.Table(nb * 128, dim, hkv.LFU, dual_bucket=True)
+    fixed = hkv.Table(nb * 128, dim, hkv.LFU, dual_bucket=True)
+    seed = w.uniform_keys(rng, int(0.9 * nb * 128), distinct=True)
+    seed_v = dev(w.normal_values(rng, seed.size, dim))
+    pooled.insert_or_assign(dev(seed), seed_v)
+    fixed.insert_or_assign(dev(seed), seed_v)
+    z = w.Zipf(1.05, 1 << 20)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for n in (20000, hkv.NOALLOC_MAX_KEYS):
+        keys = dev(z.keys(rng, n))
+        vals = dev(w.normal_values(rng, n, dim))
+        st_a, ek_a, es_a, ne_a = _outputs(n)
+        pooled.insert_or_assign(keys, vals, None, st_a, ek_a, es_a, None, ne_a)
+        st_b, ek_b, es_b, ne_b = _outputs(n)
+        rc = lib.hkv_insert_or_assign_noalloc(fixed.handle, n, _p(keys), _p(vals), None,
+                                              _p(st_b), _p(ek_b), _p(es_b), _p(ne_b), stream)
+        assert rc == 0, lib.hkv_last_error()
+        pooled.sync()
+        fixed.sync()
+        gk, gs, gv, gb = export_state(fixed)
+        b1, b2, _ = oracle.map_keys(nb, True, gk)
+        inv.check_state(gk, gs, gb, nb, b1, b2, fixed.capacity)
+        st = host(st_b)
+        assert np.all((st >= 1) & (st <= 3))
+        kb, _ = _evicted(ek_b, es_b, ne_b)
+        assert not np.any(np.isin(kb, gk)), "an evicted key is still resident"
+        ins = np.unique(host(keys)[st == hkv.ST_INSERTED])
+        assert np.all(np.isin(ins, gk)), "an inserted key is not resident"
+        a, b = pooled.size(), fixed.size()
+        assert abs(a - b) <= 0.001 * a, (a, b)
+
+
+def test_noalloc_refuses_deterministic_dual_bucket_tables():
+    lib = hkv.load_library()
+    t = hkv.Table(128 * 16, 4, hkv.LRU, dual_bucket=True, deterministic=True)
+    keys = torch.arange(1, 101, dtype=torch.int64, device="cuda")
+    vals = torch.zeros((100, 4), dtype=torch.float32, device="cuda")
+    rc = lib.hkv_insert_or_assign_noalloc(t.handle, 100, _p(keys), _p(vals), None, None, None,
+                                          None, None,
+                                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 1
+    assert b"deterministic dual-bucket" in lib.hkv_last_error()
+    assert t.size() == 0
