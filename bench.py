@@ -310,16 +310,20 @@ def measure_random_ceiling():
 # -------------------------------------------------------------------- ours
 
 def fill_table(t, lam, gen, dim, batch_fill=1 << 20, max_batches=400):
+    """Insert fresh uniform keys over the universe until the table holds
+    lam * capacity keys (0.999 * capacity for lam >= 1). Batches that cannot
+    overshoot (each adds at most batch_fill keys) run without a size check;
+    the last one is cut to the keys still missing, so a table below the
+    first-eviction load lands within a few keys of its target."""
     import torch
     from paper_2603_17168_gb300 import workloads as w
     cap = t.capacity
     target = lam * cap if lam < 1.0 else 0.999 * cap
     vals = torch.randn((batch_fill, dim), device="cuda", generator=gen)
-    done = 0
-    est = int(lam * cap / batch_fill * 0.98)
-    for _ in range(max_batches):
+    blind = max(0, int((target - t.size()) / batch_fill * 0.98))
+    for b in range(max_batches):
         k = w.uniform_keys_torch(gen, batch_fill, UNIVERSE)
-        if done >= est:
+        if b >= blind:
             size = t.size()
             if size >= target:
                 break
@@ -327,11 +331,43 @@ def fill_table(t, lam, gen, dim, batch_fill=1 << 20, max_batches=400):
             if need < batch_fill and lam < 1.0:
                 k = k[:max(need, 1)].contiguous()
         t.insert_or_assign(k, vals[:k.numel()])
-        done += 1
     return t.size() / cap
 
 
+def op_bytes(op: str, c: dict, n_calls: int, batch: int, dim: int) -> float:
+    """Algorithmic bytes of one operation kind over n_calls batches: find is
+    its kernel's bytes; insert_or_assign is the bytes of its update and
+    insert kernels (probe, in-place update, claims, victim searches) plus each
+    input key read and each status byte written once. The dedup pre-pass and
+    the reconcile / status bookkeeping are not the method's work and are left
+    out."""
+    if op == "find":
+        return kernel_bytes("find", c, n_calls, batch, dim)
+    return (kernel_bytes("update", c, n_calls, batch, dim)
+            + kernel_bytes("insert", c, n_calls, batch, dim) + n_calls * batch * (8 + 1))
+
+
+SEG_STEPS = 3        # steps per timed segment; every table is restored before each
+CONTROL_RUNS = 5     # runs of the uniform-key control per load factor (median)
+
+
+def spread(xs):
+    """(max - min) / mean of a list of positive numbers."""
+    xs = [x for x in xs if x]
+    return round((max(xs) - min(xs)) / (sum(xs) / len(xs)), 4) if xs else None
+
+
 def run_ours(args):
+    """The single-table workload. Tables are filled to just below their load
+    factor, take the W warm-up steps, are topped up to the load factor with
+    fresh uniform keys, and are then saved to device snapshots
+    (hkv_copy_state). The K timed steps run in segments of SEG_STEPS steps;
+    before each segment every table is restored from its snapshot, outside
+    the timed brackets, so each segment starts at the load factor it names
+    (the paper's median-of-runs methodology, Sec. 5.1). A profiled pass then
+    repeats the same segments on the same restored states and batches with
+    per-operation and per-kernel events; the uniform-key control runs
+    CONTROL_RUNS times per table from the snapshot."""
     import torch
     import paper_2603_17168_gb300 as hkv
     from paper_2603_17168_gb300 import workloads as w
@@ -349,31 +385,28 @@ def run_ours(args):
     nvtx = torch.cuda.nvtx
     lambdas = args.lambdas
     ceiling = None if args.no_random_access else measure_random_ceiling()
-    tables, lam_fill = [], []
+    tables = []
     nvtx.range_push("fill")
     for lam in lambdas:
         t = hkv.Table(nb * 128, DIM, hkv.LFU, dual_bucket=True)
         t.set_launch(args.find_tpk, args.update_tpk)
         if args.l2_residency:
             t.set_l2_residency(nb * 128)
-        lam_fill.append(fill_table(t, lam, gen, DIM))
+        # below the load factor by more than the warm-up steps add (each
+        # Zipf batch brings about 0.4% of the capacity in new keys)
+        pre = lam - min(0.2, 0.006 * warm + 0.01) if lam < 1.0 else lam
+        fill_table(t, max(0.0, pre), gen, DIM)
         tables.append(t)
     nvtx.range_pop()
 
     z = w.Zipf(ALPHA, UNIVERSE)
-    # warm-up batches, the headline pass, then the profiled pass
-    nbat = warm + 2 * steps
+    nbat = warm + steps
     fk = [w.zipf_keys_torch(gen, z, batch) for _ in range(nbat)]
     uk = [w.zipf_keys_torch(gen, z, batch) for _ in range(nbat)]
     uv = [torch.randn((batch, DIM), device=dev, generator=gen) for _ in range(nbat)]
     out_v = torch.empty((batch, DIM), device=dev)
     out_f = torch.empty(batch, dtype=torch.uint8, device=dev)
     out_s = torch.empty(batch, dtype=torch.uint8, device=dev)
-    torch.cuda.synchronize()
-
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.6)
 
     ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in tables]
           for _ in range(nbat)]
@@ -394,56 +427,96 @@ def run_ours(args):
         step(i)
     torch.cuda.synchronize()
     nvtx.range_pop()
-    lam_start = [t.size() / t.capacity for t in tables]
+    # top up to the load factor, then save every table's state
+    lam_fill = [fill_table(t, lam, gen, DIM) for lam, t in zip(lambdas, tables)]
+    snaps = []
+    for t in tables:
+        s = hkv.Table(nb * 128, DIM, hkv.LFU, dual_bucket=True)
+        s.copy_state_from(t)
+        snaps.append(s)
+    torch.cuda.synchronize()
+
+    def restore(which=None):
+        for li, (t, s) in enumerate(zip(tables, snaps)):
+            if which is None or li == which:
+                t.copy_state_from(s)
+
+    def lams():
+        return [t.size() / t.capacity for t in tables]
+
+    segments = []
+    i = warm
+    while i < warm + steps:
+        segments.append(range(i, min(i + SEG_STEPS, warm + steps)))
+        i += SEG_STEPS
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.6)
+
     # headline pass: the calls alone, no per-operation events or kernel
-    # profiling in the stream
-    barrier(world)
-    torch.cuda.synchronize()
-    t_wall0 = time.time()
+    # profiling in the stream; restores between segments, outside the timing
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms_local, lam_end = 0.0, [0.0] * len(tables)
+    t_wall0 = time.time()
     nvtx.range_push("timed")
-    e0.record()
-    for i in range(warm, warm + steps):
-        step(i)
-    e1.record()
+    for seg in segments:
+        restore()
+        barrier(world)
+        torch.cuda.synchronize()
+        e0.record()
+        for i in seg:
+            step(i)
+        e1.record()
+        e1.synchronize()
+        torch.cuda.synchronize()
+        barrier(world)
+        ms_local += e0.elapsed_time(e1)
+        lam_end = [max(a, b) for a, b in zip(lam_end, lams())]
     nvtx.range_pop()
-    e1.synchronize()
-    torch.cuda.synchronize()
     t_wall1 = time.time()
-    barrier(world)
-    ms_local = e0.elapsed_time(e1)
     units_local = float(steps * len(tables) * 2 * batch)
     ms, units = reduce_max_sum(ms_local, units_local, world, dev)
-    lam_end = [t.size() / t.capacity for t in tables]
 
-    # profiled pass on the next batches: per-operation events on the stream
-    # and the library's per-kernel events, with the outcome counters
-    prof_range = range(warm + steps, warm + 2 * steps)
+    # profiled pass: the same segments on the same restored states and
+    # batches, with per-operation events and the library's kernel events
     for t in tables:
         t.sync()
         t.reset_counters()
         t.profile_read()
         t.profile_enable(True)
     nvtx.range_push("profiled")
-    for i in prof_range:
-        step(i, per_op=True)
+    for seg in segments:
+        restore()
+        for i in seg:
+            step(i, per_op=True)
     torch.cuda.synchronize()
     nvtx.range_pop()
     for t in tables:
         t.profile_enable(False)
         t.sync()
+    peak, peak_src = load_peak()
 
-    # per-table, per-op times from the step events
     per_lambda = []
     for li, (lam, t) in enumerate(zip(lambdas, tables)):
-        f_ms = sum(ev[i][li][0].elapsed_time(ev[i][li][1]) for i in prof_range)
-        u_ms = sum(ev[i][li][1].elapsed_time(ev[i][li][2]) for i in prof_range)
+        f_seg = [len(seg) * batch / sum(ev[i][li][0].elapsed_time(ev[i][li][1]) for i in seg)
+                 / 1e6 for seg in segments]
+        u_seg = [len(seg) * batch / sum(ev[i][li][1].elapsed_time(ev[i][li][2]) for i in seg)
+                 / 1e6 for seg in segments]
+        f_ms = sum(ev[i][li][0].elapsed_time(ev[i][li][1]) for seg in segments for i in seg)
+        u_ms = sum(ev[i][li][1].elapsed_time(ev[i][li][2]) for seg in segments for i in seg)
         c = t.read_counters()
+        fb = op_bytes("find", c, steps, batch, DIM)
+        ub = op_bytes("upsert", c, steps, batch, DIM)
         per_lambda.append({
-            "lambda_target": lam, "lambda_fill": round(lam_fill[li], 4),
-            "lambda_start": round(lam_start[li], 4), "lambda_end": round(lam_end[li], 4),
-            "find_bkvs": round(steps * batch / f_ms / 1e6, 4),
-            "upsert_bkvs": round(steps * batch / u_ms / 1e6, 4),
+            "lambda_target": lam, "lambda_start": round(lam_fill[li], 4),
+            "lambda_end": round(lam_end[li], 4),
+            "find_bkvs": round(statistics.median(f_seg), 4),
+            "upsert_bkvs": round(statistics.median(u_seg), 4),
+            "find_frac": round(fb / (f_ms * 1e6) / peak, 4),
+            "upsert_frac": round(ub / (u_ms * 1e6) / peak, 4),
+            "find_bytes_per_key": round(fb / (steps * batch), 1),
+            "upsert_bytes_per_key": round(ub / (steps * batch), 1),
             "find_hit_rate": round(c["find_hit"] / max(1, c["find_hit"] + c["find_miss"]), 4),
             "upsert_unique": c["unique"], "updated": c["updated"], "inserted": c["inserted"],
             "evicted": c["evicted"], "rejected": c["rejected"], "retries": c["retries"],
@@ -451,7 +524,6 @@ def run_ours(args):
 
     # kernel-level roofline: device time per kernel kind from the library's
     # event brackets on the launching stream, bytes from the counters
-    peak, peak_src = load_peak()
     kinds = {}
     for li, t in enumerate(tables):
         prof = t.profile_read()
@@ -504,8 +576,62 @@ def run_ours(args):
     for e in per_lambda:
         e.pop("_counters")
 
-    # find* (pointer-returning find) on the same tables and batches, after
-    # the timed region: value copy left out, as in the paper's find* numbers
+    # uniform-key control per load factor (the paper's load-factor sweep
+    # uses uniform keys, Sec. 5.2): from the snapshot, CONTROL_RUNS runs of
+    # one find and one insert_or_assign, each batch half keys sampled
+    # uniformly from the residents and half fresh uniform keys
+    ctl_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)]
+              for _ in range(CONTROL_RUNS)]
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    res_keys = torch.empty(nb * 128, dtype=torch.int64, device=dev)
+    for li, t in enumerate(tables):
+        restore(li)
+        t.export_batch(0, nb * 128, res_keys, None, None, None, cnt)
+        n_res = int(cnt.item())
+
+        def control_batch():
+            half = batch // 2
+            pick = torch.randint(0, max(n_res, 1), (half,), device=dev, generator=gen)
+            k = torch.cat([res_keys[pick], w.uniform_keys_torch(gen, batch - half, UNIVERSE)])
+            return k[torch.randperm(batch, device=dev, generator=gen)].contiguous()
+
+        ck = [(control_batch(), control_batch()) for _ in range(CONTROL_RUNS)]
+        t.sync()
+        t.reset_counters()
+        lam_c = 0.0
+        for r, (kf, ku) in enumerate(ck):
+            restore(li)
+            ctl_ev[r][0].record()
+            t.find(kf, out_v, out_f)
+            ctl_ev[r][1].record()
+            t.insert_or_assign(ku, uv[r % nbat], status_out=out_s)
+            ctl_ev[r][2].record()
+            lam_c = max(lam_c, t.size() / t.capacity)
+        torch.cuda.synchronize()
+        c = t.read_counters()
+        f_ms = [e[0].elapsed_time(e[1]) for e in ctl_ev]
+        u_ms = [e[1].elapsed_time(e[2]) for e in ctl_ev]
+        fb = op_bytes("find", c, CONTROL_RUNS, batch, DIM)
+        ub = op_bytes("upsert", c, CONTROL_RUNS, batch, DIM)
+        per_lambda[li]["uniform"] = {
+            "find_bkvs": round(batch / statistics.median(f_ms) / 1e6, 4),
+            "upsert_bkvs": round(batch / statistics.median(u_ms) / 1e6, 4),
+            "find_frac": round(fb / (sum(f_ms) * 1e6) / peak, 4),
+            "upsert_frac": round(ub / (sum(u_ms) * 1e6) / peak, 4),
+            "find_hit_rate": round(c["find_hit"] / max(1, c["find_hit"] + c["find_miss"]), 4),
+            "lambda_end": round(lam_c, 4),
+            "evicted": c["evicted"], "rejected": c["rejected"]}
+    del res_keys
+    spreads = {"zipf": {op: spread([e[f"{op}_frac"] for e in per_lambda])
+                        for op in ("find", "upsert")},
+               "uniform": {op: spread([e["uniform"][f"{op}_frac"] for e in per_lambda])
+                           for op in ("find", "upsert")},
+               "definition": "(max - min) / mean over the load factors of each operation's "
+                             "fraction of the measured copy peak"}
+
+    # find* (pointer-returning find) on the snapshot states and the same
+    # batches: value copy left out, as in the paper's find* numbers
+    restore()
     ptrs = torch.empty(batch, dtype=torch.int64, device=dev)
     for li, t in enumerate(tables):
         t.find_ptr(fk[0], ptrs, out_f)
@@ -521,7 +647,7 @@ def run_ours(args):
     # results copied out inside the timed region
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(tables, fk, uk, uv, warm, steps, batch, world, dev, args.e2e_depth)
+        e2e = run_e2e(tables, restore, segments, fk, uk, uv, batch, world, dev, args.e2e_depth)
     clk = clocks.summary(t_wall0, t_wall1)
     clocks.stop()
 
@@ -541,12 +667,16 @@ def run_ours(args):
                        "buckets_per_table": nb, "slots_per_table": nb * 128,
                        "dim": DIM, "batch": batch, "policy": "LFU", "dual_bucket": True,
                        "lambdas": list(lambdas), "parallelism": f"replicas x{world}",
+                       "held_lambda": f"every table restored from a device snapshot "
+                                      f"(hkv_copy_state) before each segment of {SEG_STEPS} "
+                                      f"timed steps, outside the timed brackets; value = keys "
+                                      f"of all {steps} steps / summed segment times",
                        "l2": f"no flush: each table is {table_gib:.1f} GiB and a step's "
                              f"inputs {step_gib:.2f} GiB, both far above the 129 MB L2",
                        "launch": {"find_tpk": args.find_tpk or "default",
                                   "update_tpk": args.update_tpk or "default"},
                        "l2_residency_bytes": [t.l2_residency for t in tables]},
-            "per_lambda": per_lambda,
+            "per_lambda": per_lambda, "spread": spreads,
             "kernels": {k: {"ms": round(v["ms"], 4), "launches": v["launches"],
                             "share": round(v["share"], 4),
                             "gbs": round(v["gbs"], 1) if v["gbs"] else None,
@@ -555,25 +685,28 @@ def run_ours(args):
                         for k, v in sorted(kinds.items(), key=lambda kv: -kv[1]["ms"])},
             "roofline": roofline, "gpu_launches": gpu_launches, "clocks": clk, "e2e": e2e,
         }
-    for t in tables:
+    for t in tables + snaps:
         t.close()
     return result
 
 
-def run_e2e(tables, fk, uk, uv, warm, steps, batch, world, dev, depth=3):
+def run_e2e(tables, restore, segments, fk, uk, uv, batch, world, dev, depth=3):
     """The same steps end to end through the library's host-buffer pipeline
     (hkv_pipeline_*): every step's keys and rows start in page-locked host
     memory and every result (find rows and flags, upsert statuses) ends
     there; the copies of neighbouring operations overlap the kernels. Keys,
     find rows and flags and statuses cross the link whole; an upsert sends
     the rows of its distinct keys only (gathered after dedup), so those
-    bytes come from the tables' own counters over the timed steps."""
+    bytes come from the tables' own counters over the timed steps. The
+    segments and restores are those of the device-timed pass."""
     import torch
     import paper_2603_17168_gb300 as hkv
     pin = lambda x: x.cpu().pin_memory()  # noqa: E731
-    fk_h = [pin(x) for x in fk]
-    uk_h = [pin(x) for x in uk]
-    uv_h = [pin(x) for x in uv]
+    steps = sum(len(seg) for seg in segments)
+    first = segments[0][0]
+    fk_h = {i: pin(fk[i]) for seg in segments for i in seg}
+    uk_h = {i: pin(uk[i]) for seg in segments for i in seg}
+    uv_h = {i: pin(uv[i]) for seg in segments for i in seg}
     # one result buffer per table: the pipeline writes them in call order
     ov_h = [torch.empty((batch, DIM)).pin_memory() for _ in tables]
     of_h = [torch.empty(batch, dtype=torch.uint8).pin_memory() for _ in tables]
@@ -590,28 +723,32 @@ def run_e2e(tables, fk, uk, uv, warm, steps, batch, world, dev, depth=3):
                 h2d += fk_h[i].numel() * 8 + uk_h[i].numel() * 8
                 d2h += ov_h[j].numel() * 4 + of_h[j].numel() + os_h[j].numel()
 
-    for i in range(warm):
-        step(i, False)
+    restore()
+    step(first, False)   # the pipeline's first use, untimed
     pipe.sync()
     for t in tables:
         t.reset_counters()
-    torch.cuda.synchronize()
-    barrier(world)
-    t0 = time.perf_counter()
-    for i in range(warm, warm + steps):
-        step(i, True)
-    pipe.sync()
-    t1 = time.perf_counter()
-    barrier(world)
+    secs = 0.0
+    for seg in segments:
+        restore()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for i in seg:
+            step(i, True)
+        pipe.sync()
+        secs += time.perf_counter() - t0
+        barrier(world)
     pipe.close()
     for t in tables:
         h2d += t.read_counters()["unique"] * DIM * 4
-    ms, units = reduce_max_sum((t1 - t0) * 1e3, float(steps * len(tables) * 2 * batch), world, dev)
+    ms, units = reduce_max_sum(secs * 1e3, float(steps * len(tables) * 2 * batch), world, dev)
     return {"value": round(units / (ms * 1e-3) / 1e9, 4), "unit": UNIT,
             "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
             "ms_per_step": round(ms / steps, 4),
             "path": "hkv_pipeline_find / hkv_pipeline_insert_or_assign on page-locked host "
-                    f"buffers, {depth} staging slots; upsert rows of distinct keys only"}
+                    f"buffers, {depth} staging slots; upsert rows of distinct keys only; "
+                    "tables restored between segments as in the device-timed pass"}
 
 
 # -------------------------------------------------------------- the oracle
@@ -640,60 +777,166 @@ def oracle_tables(seed):
     return tabs, rng
 
 
-def oracle_step(tabs, rng, z):
+def _step_inputs(step_seed, z):
+    """One step's find keys, upsert keys and upsert rows of the oracle sample
+    (a seeded draw, so that every process draws the same ones)."""
     from paper_2603_17168_gb300 import workloads as w
-    fk = z.keys(rng, SAMPLE_OPS)
-    uk = z.keys(rng, SAMPLE_OPS)
-    uv = w.normal_values(rng, SAMPLE_OPS, DIM)
+    rng = np.random.default_rng(step_seed)
+    return z.keys(rng, SAMPLE_OPS), z.keys(rng, SAMPLE_OPS), w.normal_values(rng, SAMPLE_OPS, DIM)
+
+
+_FIND_WORKER = {}
+
+
+def _find_worker_init(seed):
+    from paper_2603_17168_gb300 import workloads as w
+    _FIND_WORKER["tabs"], _ = oracle_tables(seed)
+    _FIND_WORKER["z"] = w.Zipf(ALPHA, UNIVERSE)
+
+
+def _find_worker(task):
+    """One process's share of a step's finds on its own copy of the sample
+    tables (built from the same seed, so the same state); returns seconds."""
+    step_seed, part, parts = task
+    fk, _, _ = _step_inputs(step_seed, _FIND_WORKER["z"])
+    chunk = fk[part * fk.size // parts:(part + 1) * fk.size // parts]
     t0 = time.perf_counter()
-    for t in tabs:
-        t.find(fk)
-        t.insert_or_assign(uk, uv)
-    return time.perf_counter() - t0, 2 * SAMPLE_OPS * len(tabs)
+    for t in _FIND_WORKER["tabs"]:
+        t.find(chunk)
+    return time.perf_counter() - t0
 
 
-ORACLE_SAMPLE = (f"oracle (single-threaded C) on 4 dual-bucket LFU tables of 2^20 slots "
-                 f"(1/64 scale) at lambda 0.50/0.75/0.90/1.00, per step one find and one "
-                 f"insert_or_assign of {SAMPLE_OPS} Zipf(1.05) keys each; fill time excluded")
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OracleBaseline:
+    """The oracle timed on the host cores, with threads where the semantics
+    allow: a step's find over every core (one process per core, each with its
+    own copy of the sample tables; a step's find time is its slowest
+    process's), its dual-bucket insert_or_assign on one core (Algorithm 3 is
+    order-dependent). Like the GPU pass, every step starts from the tables'
+    state after filling: the upsert's tables are reloaded from a saved export
+    after each step, outside the timing."""
+
+    def __init__(self, seed):
+        import multiprocessing as mp
+        import concurrent.futures as cf
+        from paper_2603_17168_gb300 import workloads as w
+        self.cores = host_cores()
+        # spawn, not fork: a forked child of a process that has used the GPU hangs
+        self.pool = cf.ProcessPoolExecutor(self.cores, mp_context=mp.get_context("spawn"),
+                                           initializer=_find_worker_init, initargs=(seed,))
+        warm = [self.pool.submit(_find_worker, (1, p, self.cores)) for p in range(self.cores)]
+        self.tabs, _ = oracle_tables(seed)
+        self.saved = [t.export() for t in self.tabs]
+        self.z = w.Zipf(ALPHA, UNIVERSE)
+        for f in warm:
+            f.result()
+
+    def reload(self):
+        import oracle
+        for i, (t, st) in enumerate(zip(self.tabs, self.saved)):
+            fresh = oracle.OracleTable(t.num_buckets, t.dim, t.policy, t.dual)
+            fresh.load(*st)
+            t.close()
+            self.tabs[i] = fresh
+
+    def step(self, step_seed):
+        """(find seconds, upsert seconds, keys) of one step."""
+        parts = self.cores
+        fut = [self.pool.submit(_find_worker, (step_seed, p, parts)) for p in range(parts)]
+        _, uk, uv = _step_inputs(step_seed, self.z)
+        f_s = max(f.result() for f in fut)
+        t0 = time.perf_counter()
+        for t in self.tabs:
+            t.insert_or_assign(uk, uv)
+        u_s = time.perf_counter() - t0
+        self.reload()
+        return f_s, u_s, 2 * SAMPLE_OPS * len(self.tabs)
+
+    def close(self):
+        self.pool.shutdown()
+        for t in self.tabs:
+            t.close()
+
+
+ORACLE_SAMPLE = (f"oracle (plain C) on 4 dual-bucket LFU tables of 2^20 slots (1/64 scale) at "
+                 f"lambda 0.50/0.75/0.90/1.00, per step one find and one insert_or_assign of "
+                 f"{SAMPLE_OPS} Zipf(1.05) keys each; find split over one process per host core, "
+                 f"insert_or_assign on one core (order-dependent dual-bucket semantics); every "
+                 f"step from the filled state; fill time excluded")
+
+
+def tiny_whole_run_seconds():
+    """The tiny configuration run whole by the oracle on one core: 512
+    buckets x 128, dim 8, LRU, deterministic single-bucket, 16 batches of
+    4,096 distinct uniform keys, then 4,096 finds (2,048 resident keys and
+    2,048 fresh ones)."""
+    import oracle
+    from paper_2603_17168_gb300 import workloads as w
+    rng = np.random.default_rng(w.seed_for(1))
+    batches = [w.uniform_keys(rng, 4096, distinct=True) for _ in range(16)]
+    vals = [w.normal_values(rng, 4096, 8) for _ in range(16)]
+    t0 = time.perf_counter()
+    t = oracle.OracleTable(512, 8, oracle.LRU)
+    for k, v in zip(batches, vals):
+        t.insert_or_assign(k, v, deterministic=True)
+    res = t.export()[0]
+    q = np.concatenate([rng.choice(res, 2048, replace=False), w.uniform_keys(rng, 2048)])
+    t.find(q)
+    secs = time.perf_counter() - t0
+    t.close()
+    return secs
+
+
+def time_oracle(steps, warmup=1):
+    from paper_2603_17168_gb300 import workloads as w
+    base = OracleBaseline(w.seed_for(2, 99))
+    try:
+        for i in range(warmup):
+            base.step(w.seed_for(2, 1000 + i))
+        f_s = u_s = units = 0
+        for i in range(steps):
+            a, b, u = base.step(w.seed_for(2, 2000 + i))
+            f_s += a
+            u_s += b
+            units += u
+    finally:
+        base.close()
+    secs = f_s + u_s
+    return {"value": round(units / secs / 1e9, 6), "unit": UNIT, "cores": base.cores,
+            "kind": "oracle", "secs": secs,
+            "find_bkvs": round(units / 2 / f_s / 1e9, 6),
+            "upsert_bkvs": round(units / 2 / u_s / 1e9, 6),
+            "sample": ORACLE_SAMPLE + f", {steps} timed steps ({secs:.1f} s of timed work)"}
 
 
 def cpu_baseline(steps=24):
-    from paper_2603_17168_gb300 import workloads as w
-    tabs, rng = oracle_tables(w.seed_for(2, 99))
-    z = w.Zipf(ALPHA, UNIVERSE)
-    oracle_step(tabs, rng, z)
-    secs = units = 0
-    for _ in range(steps):
-        s, u = oracle_step(tabs, rng, z)
-        secs += s
-        units += u
-    return {"value": round(units / secs / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": ORACLE_SAMPLE + f", {steps} timed steps ({secs:.1f} s)"}
+    r = time_oracle(steps)
+    r.pop("secs")
+    r["cfg1_s"] = round(tiny_whole_run_seconds(), 4)
+    r["cfg1_note"] = "the tiny configuration's whole run (16 upsert batches and the finds), 1 core"
+    return r
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return None
-    from paper_2603_17168_gb300 import workloads as w
-    tabs, rng = oracle_tables(w.seed_for(2, 99))
-    z = w.Zipf(ALPHA, UNIVERSE)
-    for _ in range(args.warmup):
-        oracle_step(tabs, rng, z)
-    secs = units = 0
-    for _ in range(args.steps):
-        s, u = oracle_step(tabs, rng, z)
-        secs += s
-        units += u
-    value = units / secs / 1e9
-    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+    r = time_oracle(args.steps, args.warmup)
+    secs = r.pop("secs")
+    value = r["value"]
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(secs * 1e3 / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD + " (oracle sample, see cpu_baseline)"},
-            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1,
-                             "kind": "oracle", "sample": ORACLE_SAMPLE},
-            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+            "cpu_baseline": r,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
 

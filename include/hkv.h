@@ -3,10 +3,11 @@
  * the data-parallel hot path of HierarchicalKV (arxiv 2603.17168).
  *
  * A table is a power-of-two number B of buckets of S = 128 slots. Each
- * bucket keeps, in HBM, a 128-byte line of 8-bit digests (one per slot),
- * 128 uint64 keys and 128 uint64 scores; values (dim fp32 each) live in a
- * separate arena addressed by (bucket, slot), spilling past an HBM budget
- * into pinned host memory (Sec. 3.2, Fig. 4; Sec. 3.6; Sec. 4.2).
+ * bucket keeps, in HBM, a 128-byte line of 8-bit digests (one per slot) and
+ * a 2 KiB run of 128 (uint64 key, uint64 score) pairs, each pair one
+ * 16-byte unit; values (dim fp32 each) live in a separate arena addressed by
+ * (bucket, slot), spilling past an HBM budget into pinned host memory
+ * (Sec. 3.2, Fig. 4; Sec. 3.6; Sec. 4.2).
  *
  * Conventions for every call below:
  *  - Array arguments are DEVICE pointers (or pinned, mapped host pointers
@@ -190,11 +191,15 @@ hkv_status hkv_insert_or_assign(hkv_table_t t, uint64_t n, const uint64_t *keys,
  *               with HKV_ERR_INVALID_ARG (split them, or use the pooled call).
  *   the table's device must be current.
  * Every GPU that loads the library holds the 5 MiB array until the process
- * exits. The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * exits. Each call looks up the array's device address in the current
+ * context (cudaGetSymbolAddress); the first lookup on a device may load the
+ * library's device code there, so make the first call on each device before
+ * any stream capture.
  * All calls on a device share the one array, and each call overwrites it:
  * calls that can overlap on that GPU (issued on different streams, even for
- * different tables) race and must be ordered by the caller. Other
+ * different tables) race and must be ordered by the caller.
+ * Deterministic dual-bucket tables are refused with HKV_ERR_INVALID_ARG
+ * (their ordered waves need pool scratch; use hkv_insert_or_assign). Other
  * arguments and results are as in hkv_insert_or_assign. */
 #define HKV_NOALLOC_MAX_KEYS 65536u
 hkv_status hkv_insert_or_assign_noalloc(hkv_table_t t, uint64_t n, const uint64_t *keys,
@@ -248,6 +253,21 @@ hkv_status hkv_export_batch_if(hkv_table_t t, uint64_t slot_offset, uint64_t n_s
                                uint64_t score_min, uint64_t score_max, uint64_t *count_out,
                                uint64_t *keys, float *values, uint64_t *scores, uint64_t *slots,
                                hkv_stream_t stream);
+
+/* copy_state (inserter on dst, reader on src): make dst a copy of src -
+ * digests, (key, score) pairs, per-bucket occupancy, every value slice, and
+ * the host-side step and epoch - with stream-ordered device-to-device
+ * copies on `stream` (host slices copied host to host). The paper has no
+ * such call: its evaluation reports the median of repeated runs from one
+ * table state (Sec. 5.1), and this is how a caller restores that state
+ * between runs, or keeps a checkpoint of a table on the device.
+ *   dst, src  distinct tables created with the same capacity, dim, policy,
+ *             dual_bucket, deterministic, value budget and slice size, on
+ *             the same device; otherwise HKV_ERR_INVALID_ARG and nothing
+ *             is copied.
+ * Counters, profiling records, launch shapes and the L2 window of dst are
+ * kept. Cost: one read and one write of each table's bytes. */
+hkv_status hkv_copy_state(hkv_table_t dst, hkv_table_t src, hkv_stream_t stream);
 
 /* Step and epoch used by the score policies (see hkv_policy). Host-side
  * state: apply to calls issued after this one. */

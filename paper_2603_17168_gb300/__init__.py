@@ -69,6 +69,7 @@ SIGNATURES = {
     "hkv_assign": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp]),
     "hkv_erase": (_i32, [_vp, _u64, _vp, _vp]),
     "hkv_size": (_i32, [_vp, _P64, _vp]),
+    "hkv_copy_state": (_i32, [_vp, _vp, _vp]),
     "hkv_export_batch": (_i32, [_vp, _u64, _u64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hkv_set_step": (_i32, [_vp, _u64]),
     "hkv_get_step": (_u64, [_vp]),
@@ -346,6 +347,10 @@ class Table:
         _check(load_library().hkv_erase(self._h, keys.numel(), _ptr(keys), _stream(stream)))
 
     # ---------------------------------------------------------------- state
+    def copy_state_from(self, src: "Table", stream=None):
+        """Make this table a copy of `src` (same shape): see hkv_copy_state."""
+        _check(load_library().hkv_copy_state(self.handle, src.handle, _stream(stream)))
+
     def set_step(self, step: int):
         _check(load_library().hkv_set_step(self._h, step))
 

@@ -443,6 +443,42 @@ hkv_status hkv_erase(hkv_table_t t, uint64_t n, const uint64_t* keys, hkv_stream
   return rc;
 }
 
+hkv_status hkv_copy_state(hkv_table_t dst, hkv_table_t src, hkv_stream_t stream) {
+  if (bad(dst) || bad(src) || dst == src)
+    return fail(HKV_ERR_INVALID_ARG, "copy_state: two distinct tables");
+  const hkv_options &a = dst->opts, &b = src->opts;
+  if (dst->capacity != src->capacity || a.dim != b.dim || a.policy != b.policy ||
+      a.dual_bucket != b.dual_bucket || a.deterministic != b.deterministic ||
+      dst->slots_per_slice != src->slots_per_slice ||
+      dst->hbm_slices.size() != src->hbm_slices.size() ||
+      dst->host_slices.size() != src->host_slices.size() || dst->device != src->device)
+    return fail(HKV_ERR_INVALID_ARG, "copy_state: tables of different shapes");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // Take the two roles in address order, so that two threads copying in
+  // opposite directions cannot wait on each other.
+  hkv_table_s* first = dst < src ? dst : src;
+  hkv_table_s* second = dst < src ? src : dst;
+  auto l1 = first->sched.acquire(first == dst ? kInserter : kReader, s);
+  auto l2 = second->sched.acquire(second == dst ? kInserter : kReader, s);
+  // digests, (key, score) pairs and occupancy counters: the metadata up to
+  // the error word, which sits at the same offset in both tables
+  const uint64_t meta = reinterpret_cast<const char*>(src->dev.err) -
+                        reinterpret_cast<const char*>(src->meta);
+  cudaMemcpyAsync(dst->meta, src->meta, meta, cudaMemcpyDeviceToDevice, s);
+  const uint64_t slice_bytes = src->slots_per_slice * (uint64_t)b.dim * 4;
+  for (size_t i = 0; i < src->hbm_slices.size(); ++i)
+    cudaMemcpyAsync(dst->hbm_slices[i], src->hbm_slices[i], slice_bytes,
+                    cudaMemcpyDeviceToDevice, s);
+  for (size_t i = 0; i < src->host_slices.size(); ++i)
+    cudaMemcpyAsync(dst->host_slices[i], src->host_slices[i], slice_bytes, cudaMemcpyDefault, s);
+  dst->step = src->step;
+  dst->epoch = src->epoch;
+  const hkv_status rc = cuda_status(cudaGetLastError(), "copy_state");
+  second->sched.release(s);
+  first->sched.release(s);
+  return rc;
+}
+
 hkv_status hkv_size(hkv_table_t t, uint64_t* out, hkv_stream_t stream) {
   if (bad(t) || !out) return fail(HKV_ERR_INVALID_ARG, "size arguments");
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -73,3 +73,31 @@ def test_workload_name_follows_the_sizes():
     assert small.startswith("single table x1 (lambda 0.50): 2^24 slots (2^17 buckets x 128)")
     assert "2^18 Zipf(1.05)" in small
     assert "3000 Zipf" in bench.single_workload(17, 3000, (0.5, 1.0))
+
+
+def test_upsert_op_bytes_leave_out_dedup_and_bookkeeping():
+    c = counters(unique=500, updated=300, inserted=200, upd_claims=200, upd_lines=500,
+                 evicted=5, rejected=3)
+    n = 1000
+    ob = bench.op_bytes("upsert", c, 1, n, 32)
+    # the update and insert kernels' work plus one key read and one status
+    # byte per input key; dedup, reconcile and status kernels are not counted
+    assert ob == (bench.kernel_bytes("update", c, 1, n, 32)
+                  + bench.kernel_bytes("insert", c, 1, n, 32) + n * 9)
+    assert bench.op_bytes("find", c, 1, n, 32) == bench.kernel_bytes("find", c, 1, n, 32)
+
+
+def test_spread_is_range_over_mean():
+    assert bench.spread([0.5, 0.5, 0.5]) == 0.0
+    assert bench.spread([0.4, 0.6]) == 0.4
+    assert bench.spread([None, 0.3, 0.3]) == 0.0
+    assert bench.spread([]) is None
+
+
+def test_oracle_baseline_splits_find_over_cores_and_times_the_tiny_run():
+    """The CPU baseline's find work is split over processes that each rebuild
+    the same sample tables; two steps of it run here on the host."""
+    r = bench.time_oracle(steps=1, warmup=0)
+    assert r["kind"] == "oracle" and r["cores"] >= 1 and r["value"] > 0
+    assert r["find_bkvs"] > 0 and r["upsert_bkvs"] > 0
+    assert 0 < bench.tiny_whole_run_seconds() < 60
