@@ -382,13 +382,20 @@ __device__ __forceinline__ void claim_backoff(int attempt, uint64_t h) {
 // per-bucket counters, which count a slot from the moment its claim CAS
 // succeeds, so a counter never exceeds the slots really taken: a counter at
 // 128 means full, and a bucket whose counter lags behind its digests is
-// simply scanned again. Returns 0 when the key was placed (or the bounded
-// wait ran out and the error was latched), 2 when every candidate bucket
-// is full and the key needs a victim search.
-template <bool VEC16>
+// simply scanned again. The thread writes the slot's digest, score and key;
+// the caller's lane group then copies the value row into slot `g_out`
+// (phase U has no reader of a claimed slot's value, and the kernel boundary
+// orders the row before phase I). One thread storing a whole row issues
+// half-sector stores to 32 rows per instruction, which cost the update
+// kernel 40% of its time; a group's lanes write whole sectors. Returns 0
+// when the key was placed (g_out = its global slot; or the bounded wait ran
+// out, the error was latched and g_out = kNoSlot), 2 when every candidate
+// bucket is full and the key needs a victim search.
+constexpr uint64_t kNoSlot = ~0ull;
+
 __device__ __forceinline__ uint8_t claim_free_slot(const TableDev& t, const Scratch& s, uint32_t e,
                                                    uint64_t key, uint64_t h, uint64_t sc,
-                                                   const float* src, unsigned& sectors,
+                                                   uint64_t& g_out, unsigned& sectors,
                                                    unsigned& inserted, unsigned& retries) {
   const uint64_t b1 = h & t.bucket_mask;
   const uint64_t b2 = t.dual ? second_bucket(t, key) : b1;
@@ -411,7 +418,10 @@ __device__ __forceinline__ uint8_t claim_free_slot(const TableDev& t, const Scra
       continue;
     }
     atomicAdd(t.sizes + b, 1u);
-    fill_slot_thread<VEC16, false>(t, g, key, sc, digest_from_hash(h), src);
+    t.digests[g] = (uint8_t)digest_from_hash(h);
+    __stcg(reinterpret_cast<unsigned long long*>(score_ptr(t, g)), (unsigned long long)sc);
+    __stcg(reinterpret_cast<unsigned long long*>(key_ptr(t, g)), (unsigned long long)key);
+    g_out = g;
     s.tstatus[e] = HKV_ST_INSERTED;
     inserted++;
     return 0;
@@ -514,6 +524,7 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
       }
     }
     const bool hit = active && slot >= 0;
+    uint64_t gclaim = kNoSlot;
     if (active) {
       if (hit) {
         const uint64_t g = b * kSlots + (uint64_t)slot;
@@ -539,8 +550,7 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
         } else if (!hit) {
           const uint64_t sc = policy_score(t.policy, false, 0, m, scores_in != nullptr,
                                            scores_in ? __ldg(scores_in + i) : 0, ctx);
-          flag = claim_free_slot<VEC16>(t, s, e, key, h, sc, values + i * t.dim, ins_lines,
-                                        inserted, retries);
+          flag = claim_free_slot(t, s, e, key, h, sc, gclaim, ins_lines, inserted, retries);
         }
         s.mflag[u] = flag;
         if (flag) {
@@ -549,6 +559,11 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
           deferred++;
         }
       }
+    }
+    if (UPSERT) {
+      // the row of a slot claimed above, copied by the key's G lanes
+      const uint64_t gc = __shfl_sync(kFull, gclaim, group_base);
+      if (gc != kNoSlot) copy_row<G, VEC16, false>(value_ptr(t, gc), values + i * t.dim, t.dim, lane_g);
     }
   }
   const int which[7] = {HKV_CNT_UPDATED, HKV_CNT_UPD_LINES, HKV_CNT_UPD_KEYS, HKV_CNT_INSERTED,
