@@ -1167,14 +1167,63 @@ SERVE_WORKLOAD = ("serving: the 8 multi-table tables (LRU, pre-filled to lambda 
                   "results to pinned host memory")
 
 
-def _latency_stats(items, res):
+def _latency_stats(items, res, stats=None):
     lat = np.array([(r.done_s - it["arrival_s"]) * 1e3 for r, it in zip(res, items)])
     span = max(r.done_s for r in res) - min(it["arrival_s"] for it in items)
     keys = sum(int(it["keys"].numel()) for it in items)
-    return {"p50_ms": round(float(np.percentile(lat, 50)), 3),
-            "p99_ms": round(float(np.percentile(lat, 99)), 3),
-            "bkvs": round(keys / span / 1e9, 4), "requests": len(items),
-            "rounds": len({r.round for r in res})}
+    out = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+           "p99_ms": round(float(np.percentile(lat, 99)), 3),
+           "bkvs": round(keys / span / 1e9, 4), "requests": len(items),
+           "rounds": len({r.round for r in res})}
+    if stats:
+        # where the run's time went: host loop phases, device busy time, and
+        # the host link's load (bytes each way over the run's wall time)
+        w_s = max(stats["wall_s"], 1e-9)
+        out["breakdown"] = {
+            "wall_s": round(stats["wall_s"], 3),
+            "host_admit_s": round(stats["host_admit_s"], 3),
+            "host_launch_s": round(stats["host_launch_s"], 3),
+            "host_retire_s": round(stats["host_retire_s"], 3),
+            "host_idle_s": round(stats["idle_s"], 3),
+            "gpu_compute_s": round(stats["gpu_compute_s"], 3),
+            "gpu_copy_out_s": round(stats["gpu_copy_out_s"], 3),
+            "direct_rounds": stats["direct_rounds"], "batched_rounds": stats["batched_rounds"],
+            "h2d_gbs": round(stats["h2d_bytes"] / w_s / 1e9, 2),
+            "d2h_gbs": round(stats["d2h_bytes"] / w_s / 1e9, 2)}
+    return out
+
+
+def measure_link(nbytes=1 << 28, reps=5):
+    """Host link bandwidth between page-locked host memory and HBM, in GB/s:
+    host to device, device to host, and both at once (two streams), best of
+    `reps` copies of nbytes each way, timed with CUDA events."""
+    import torch
+    h_in = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h_out = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d_a = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d_b = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    best = {"h2d": 0.0, "d2h": 0.0, "both": 0.0}
+    for _ in range(reps):
+        for kind in best:
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            if kind in ("h2d", "both"):
+                s1.wait_event(a)
+                with torch.cuda.stream(s1):
+                    d_a.copy_(h_in, non_blocking=True)
+            if kind in ("d2h", "both"):
+                s2.wait_event(a)
+                with torch.cuda.stream(s2):
+                    h_out.copy_(d_b, non_blocking=True)
+            torch.cuda.current_stream().wait_stream(s1)
+            torch.cuda.current_stream().wait_stream(s2)
+            b.record()
+            b.synchronize()
+            moved = nbytes * (2 if kind == "both" else 1)
+            best[kind] = max(best[kind], moved / (a.elapsed_time(b) * 1e-3) / 1e9)
+    return {k: round(v, 1) for k, v in best.items()}
 
 
 def run_serve(args):
@@ -1211,6 +1260,15 @@ def run_serve(args):
         flags = torch.empty(n, dtype=torch.uint8).pin_memory()
         pool.append(dict(table=tab, op=op, keys=keys, values=vals, flags=flags))
     mean_n = float(np.mean([p["keys"].numel() for p in pool]))
+    # bytes each request moves over the host link, per key of the pool
+    keys_total = sum(p["keys"].numel() for p in pool)
+    h2d_pk = sum(p["keys"].numel() * 8 + (p["values"].numel() * 4 if p["op"] == hkv.OP_UPSERT
+                                          else 0) for p in pool) / keys_total
+    d2h_pk = sum(p["keys"].numel() + (p["values"].numel() * 4 if p["op"] == hkv.OP_FIND else 0)
+                 for p in pool) / keys_total
+    link = measure_link()
+    link_bound = min(link["h2d"] * 1e9 / h2d_pk, link["d2h"] * 1e9 / d2h_pk,
+                     link["both"] * 1e9 / (h2d_pk + d2h_pk)) / 1e9
 
     def make(n_req, rate):
         items, t = [], 0.0
@@ -1222,15 +1280,30 @@ def run_serve(args):
             items.append(it)
         return items
 
+    def run(items, reqs, batched):
+        res = srv.run(reqs, batched=batched)
+        return _latency_stats(items, res, srv.stats())
+
     # warm the graphs and the pipeline
     warm = make(min(256, len(pool)), 0)
     srv.run(hkv.make_requests(warm), batched=True)
     srv.run(hkv.make_requests(warm[:64]), batched=False)
     # peak: closed loop, every request queued at t = 0
     peak_items = make(args.serve_peak_requests, 0)
-    peak_b = _latency_stats(peak_items, srv.run(hkv.make_requests(peak_items), batched=True))
-    peak_p = _latency_stats(peak_items, srv.run(hkv.make_requests(peak_items), batched=False))
+    peak_reqs = hkv.make_requests(peak_items)
+    peak_b = run(peak_items, peak_reqs, True)
+    peak_p = run(peak_items, peak_reqs, False)
     peak_keys_s = peak_b["bkvs"] * 1e9
+    # the same closed loops with every round timed on the device, for the
+    # breakdown only (the timing events cost host time of their own)
+    srv.profile(True)
+    srv.run(peak_reqs, batched=True)
+    peak_b["profiled"] = _latency_stats(peak_items, srv.run(peak_reqs, batched=True),
+                                        srv.stats())["breakdown"]
+    srv.run(peak_reqs, batched=False)
+    peak_p["profiled"] = _latency_stats(peak_items, srv.run(peak_reqs, batched=False),
+                                        srv.stats())["breakdown"]
+    srv.profile(False)
     served = {}
     for frac in (0.25, 0.50, 0.90):
         rate = frac * peak_keys_s / mean_n
@@ -1239,8 +1312,8 @@ def run_serve(args):
         reqs = hkv.make_requests(items)
         served[f"{int(frac * 100)}%"] = {
             "offered_bkvs": round(frac * peak_keys_s / 1e9, 4),
-            "batched": _latency_stats(items, srv.run(reqs, batched=True)),
-            "plain": _latency_stats(items, srv.run(reqs, batched=False))}
+            "batched": run(items, reqs, True),
+            "plain": run(items, reqs, False)}
     srv.close()
     for t in tables:
         t.close()
@@ -1254,6 +1327,9 @@ def run_serve(args):
                        "ring_keys_per_table": 1 << 20, "max_inflight_rounds": 3,
                        "request_pool": len(pool), "mean_request_keys": round(mean_n),
                        "seconds_per_load": args.serve_seconds,
+                       "link_bytes_per_key": {"h2d": round(h2d_pk, 1), "d2h": round(d2h_pk, 1)},
+                       "link_gbs": link,
+                       "link_bound_bkvs": round(link_bound, 4),
                        "step": "a request; value = closed-loop peak of the batched loop"},
             "peak": {"batched": peak_b, "plain": peak_p}, "served": served}
 

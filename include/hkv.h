@@ -391,12 +391,22 @@ hkv_status hkv_batch_destroy(hkv_batch_t b);
  * launch (hkv_batch_run, with use_graph), copies each request's results
  * back to its host buffers and records a completion event. Every request
  * therefore sees its table exactly as it would alone, in arrival order.
+ * A round with one busy table calls that table's hkv_find /
+ * hkv_insert_or_assign directly instead (grids sized to the request). The
+ * results of batched rounds travel back on a copy-out stream of the server,
+ * so the next round's kernels overlap them, and every request has its own
+ * completion event.
  * With batched = 0 the same trace runs one request at a time through
- * hkv_find / hkv_insert_or_assign, oldest first (the plain path).
+ * hkv_find / hkv_insert_or_assign, oldest first, results copied back on
+ * `stream` (the plain path).
  * Synchronous: returns when every request has completed; results[i] gets
  * the admission and completion times (seconds since the run started,
- * host clock, completion stamped by polling the round's event) and the
- * round that carried it. Find rows of misses are left unspecified. */
+ * host clock, completion stamped by polling the request's event) and the
+ * round that carried it. Find rows of misses are left unspecified.
+ * hkv_serve_stats_get copies out where the last run spent its time; the
+ * device-time fields are filled only while hkv_serve_profile(s, 1) is on,
+ * which brackets every round with timing events (host time of their own,
+ * so latency runs leave it off). */
 typedef struct hkv_server_s *hkv_server_t;
 typedef struct {
   double arrival_s;        /* seconds from the start of the run; non-decreasing */
@@ -419,6 +429,23 @@ uint64_t hkv_serve_hbm_bytes(hkv_server_t s);
 hkv_status hkv_serve_run(hkv_server_t s, const hkv_serve_request *reqs, uint64_t n_req,
                          int batched, int use_graph, hkv_serve_result *results,
                          hkv_stream_t stream);
+typedef struct {
+  double wall_s;          /* start of the run to its last completion */
+  double host_admit_s;    /* host loop: admitting arrivals, issuing their input copies */
+  double host_launch_s;   /* host loop: forming rounds, launching them, issuing copies back */
+  double host_retire_s;   /* host loop: polling completion events, retiring requests */
+  double idle_s;          /* host loop: yielding with nothing to do */
+  double gpu_compute_s;   /* device time of the rounds' kernels on `stream` (profiling on) */
+  double gpu_copy_out_s;  /* device time of the copies back to the host (profiling on) */
+  uint64_t requests;
+  uint64_t direct_rounds;   /* rounds run through one table's own call */
+  uint64_t batched_rounds;  /* rounds run through hkv_batch_run */
+  uint64_t loop_iterations;
+  uint64_t h2d_bytes;       /* request keys and upsert rows copied in */
+  uint64_t d2h_bytes;       /* find rows and flags copied back */
+} hkv_serve_stats;
+hkv_status hkv_serve_stats_get(hkv_server_t s, hkv_serve_stats *out);
+hkv_status hkv_serve_profile(hkv_server_t s, int on);
 hkv_status hkv_serve_destroy(hkv_server_t s);
 
 /* Host-buffer pipeline (the paper has no host API; this is the library's

@@ -55,6 +55,14 @@ class ServeRequest(ctypes.Structure):
 class ServeResult(ctypes.Structure):
     _fields_ = [("admit_s", ctypes.c_double), ("done_s", ctypes.c_double), ("round", _u64)]
 
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("wall_s", "host_admit_s", "host_launch_s",
+                                               "host_retire_s", "idle_s", "gpu_compute_s",
+                                               "gpu_copy_out_s")] + \
+               [(n, _u64) for n in ("requests", "direct_rounds", "batched_rounds",
+                                    "loop_iterations", "h2d_bytes", "d2h_bytes")]
+
 SIGNATURES = {
     "hkv_create": (_i32, [ctypes.POINTER(Options), ctypes.POINTER(_vp)]),
     "hkv_destroy": (_i32, [_vp]),
@@ -93,6 +101,8 @@ SIGNATURES = {
     "hkv_serve_run": (_i32, [_vp, ctypes.POINTER(ServeRequest), _u64, _i32, _i32,
                              ctypes.POINTER(ServeResult), _vp]),
     "hkv_serve_destroy": (_i32, [_vp]),
+    "hkv_serve_stats_get": (_i32, [_vp, ctypes.POINTER(ServeStats)]),
+    "hkv_serve_profile": (_i32, [_vp, _i32]),
     "hkv_pipeline_create": (_i32, [_u64, _u32, _i32, ctypes.POINTER(_vp)]),
     "hkv_pipeline_find": (_i32, [_vp, _vp, _u64, _vp, _vp, _vp]),
     "hkv_pipeline_insert_or_assign": (_i32, [_vp, _vp, _u64, _vp, _vp, _vp, _vp]),
@@ -568,6 +578,16 @@ class Server:
         _check(load_library().hkv_serve_run(self._h, requests, n, int(batched), int(use_graph),
                                             res, _stream(stream)))
         return res
+
+    def profile(self, on: bool = True):
+        """Time every round on the device in later runs (hkv_serve_profile)."""
+        _check(load_library().hkv_serve_profile(self._h, int(on)))
+
+    def stats(self) -> dict:
+        """Where the last run() spent its time (hkv_serve_stats)."""
+        st = ServeStats()
+        _check(load_library().hkv_serve_stats_get(self._h, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in ServeStats._fields_}
 
 
 def make_requests(items):

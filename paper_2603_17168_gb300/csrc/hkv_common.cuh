@@ -22,6 +22,10 @@
 
 #include "../../include/hkv.h"
 
+#ifndef HKV_COPY_ROW_R
+#define HKV_COPY_ROW_R 1
+#endif
+
 namespace hkv {
 
 constexpr uint32_t kSlots = 128;
@@ -284,13 +288,30 @@ __device__ __noinline__ int probe_rest(const uint8_t* line, const uint64_t* kb, 
 // pays off in kernels with few warps per SM to hide latency (the update
 // phase); at full occupancy the one-pass form, which confirms each match as
 // it meets it, issues fewer instructions (find).
-template <int G, bool CG, bool TWO_PASS>
+//
+// FREE (two-pass form only): the digest words the probe already holds also
+// give the bucket's free slots (digest byte 0) as they were when the line
+// was read. *fi receives, on every lane of the group, their number and one
+// of them packed as free_info(count, slot), slot -1 when there is none: the
+// group lane `pick >> 8` (mod G) offers it, the free byte of its share
+// nearest to word `pick & 255` (mod 32/G), so keys claiming in one bucket
+// tend to pick different slots. (One packed word keeps the update kernel
+// within its register budget.)
+__device__ __forceinline__ unsigned free_info(int count, int slot) {
+  return ((unsigned)count << 8) | (unsigned)(slot + 1);
+}
+__device__ __forceinline__ int free_count(unsigned fi) { return (int)(fi >> 8); }
+__device__ __forceinline__ int free_slot_of(unsigned fi) { return (int)(fi & 255u) - 1; }
+
+template <int G, bool CG, bool TWO_PASS, bool FREE = false>
 __device__ __forceinline__ int probe_bucket(const TableDev& t, uint64_t b, uint64_t key,
                                             uint32_t pat4, bool active, int lane_g,
                                             unsigned group_bits, int group_base,
-                                            unsigned& key_reads) {
+                                            unsigned& key_reads, unsigned pick = 0,
+                                            unsigned* fi = nullptr) {
   constexpr int W = 32 / G;
   int my = -1;
+  int nfree = 0, free_slot = -1;
   if (active && !TWO_PASS) {
     uint32_t w[W];
     load_line<G, CG>(t.digests + b * kSlots, lane_g, w);
@@ -322,6 +343,7 @@ __device__ __forceinline__ int probe_bucket(const TableDev& t, uint64_t b, uint6
     {
       uint32_t w[W];
       load_line<G, CG>(line, lane_g, w);
+      int best = W;  // distance of free_slot's word from the start word
 #pragma unroll
       for (int q = 0; q < W; ++q) {
         const uint32_t m = match4(w[q], pat4);
@@ -331,6 +353,15 @@ __device__ __forceinline__ int probe_bucket(const TableDev& t, uint64_t b, uint6
           push(sa);
           if (sb != sa) push(sb);
           more |= __popc(m) > 16;
+        }
+        if constexpr (FREE) {
+          const uint32_t z = __vcmpeq4(w[q], 0u);
+          nfree += __popc(z) >> 3;
+          const int d = (q - (int)(pick & 255u)) & (W - 1);
+          if (z && d < best) {
+            best = d;
+            free_slot = first + q * 4 + ((__ffs(z) - 1) >> 3);
+          }
         }
       }
     }
@@ -347,20 +378,43 @@ __device__ __forceinline__ int probe_bucket(const TableDev& t, uint64_t b, uint6
   const unsigned bal = __ballot_sync(0xFFFFFFFFu, my >= 0) & group_bits;
   const int src = bal ? __ffs(bal) - 1 : group_base;
   const int slot = __shfl_sync(0xFFFFFFFFu, my, src);
+  if constexpr (FREE) {
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) nfree += __shfl_xor_sync(0xFFFFFFFFu, nfree, o);
+    // the offering lane: the first lane with a free byte from lane pick >> 8
+    const unsigned offer = __ballot_sync(0xFFFFFFFFu, free_slot >= 0) & group_bits;
+    const unsigned rel = G == 32 ? offer : (offer >> group_base) & ((1u << G) - 1u);
+    const int rot = (int)((pick >> 8) & (unsigned)(G - 1));
+    const uint64_t twice = (uint64_t)rel | ((uint64_t)rel << G);  // rotation without wrap
+    const uint64_t from = twice >> rot;
+    const int off = from ? (__ffsll((long long)from) - 1 + rot) & (G - 1) : 0;
+    const int fs = __shfl_sync(0xFFFFFFFFu, free_slot, group_base + off);
+    *fi = free_info(nfree, offer ? fs : -1);
+  }
   return bal ? slot : -1;
 }
 
 // Copy one value row of `dim` floats with G cooperating lanes, using 16-byte
 // vectors when VEC16 (dim % 4 == 0 and 16-byte aligned rows), else 4-byte.
-template <int G, bool VEC16, bool STREAM_DST>
+// Each lane issues R loads before it stores them, so a row costs one memory
+// latency per R vectors per lane rather than one per vector (rows in mapped
+// host memory are a link round trip away).
+template <int G, bool VEC16, bool STREAM_DST, int R = HKV_COPY_ROW_R>
 __device__ __forceinline__ void copy_row(float* dst, const float* src, uint32_t dim, int lane_g) {
   if constexpr (VEC16) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
     float4* d4 = reinterpret_cast<float4*>(dst);
-    uint32_t n4 = dim >> 2;
-    for (uint32_t j = lane_g; j < n4; j += G) {
-      float4 v = __ldg(s4 + j);
-      if (STREAM_DST) __stcs(d4 + j, v); else d4[j] = v;
+    const uint32_t n4 = dim >> 2;
+    for (uint32_t j0 = lane_g; j0 < n4; j0 += R * G) {
+      float4 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (j0 + r * G < n4) v[r] = __ldg(s4 + j0 + r * G);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (j0 + r * G >= n4) break;
+        if (STREAM_DST) __stcs(d4 + j0 + r * G, v[r]); else d4[j0 + r * G] = v[r];
+      }
     }
   } else {
     for (uint32_t j = lane_g; j < dim; j += G) {

@@ -393,6 +393,48 @@ __device__ __forceinline__ void claim_backoff(int attempt, uint64_t h) {
 // bucket is full and the key needs a victim search.
 constexpr uint64_t kNoSlot = ~0ull;
 
+// The writes of a claim that won slot g of bucket b (key word LOCKED): the
+// bucket's count, digest, score, then the key.
+__device__ __forceinline__ void write_claimed(const TableDev& t, uint64_t b, uint64_t g,
+                                              uint64_t key, uint64_t h, uint64_t sc) {
+  atomicAdd(t.sizes + b, 1u);
+  t.digests[g] = (uint8_t)digest_from_hash(h);
+  __stcg(reinterpret_cast<unsigned long long*>(score_ptr(t, g)), (unsigned long long)sc);
+  __stcg(reinterpret_cast<unsigned long long*>(key_ptr(t, g)), (unsigned long long)key);
+}
+
+// First claim attempt of a missing key, from the digest lines its probe
+// read (Algorithm 3 phase D1 on the free counts the probe saw: the bucket
+// with more free slots, b1 on a tie): a CAS on the free slot the probe
+// offered, with no further reads. Returns 0 when the key was placed (g_out
+// set), 2 when both candidates were full at the probe (no slot is freed
+// during a batch, so they still are), 1 when the CAS lost and the caller
+// must claim through the occupancy counters (claim_free_slot).
+__device__ __forceinline__ uint8_t claim_probed_slot(const TableDev& t, const Scratch& s,
+                                                     uint32_t e, uint64_t key, uint64_t h,
+                                                     uint64_t sc, uint64_t b1, unsigned f1,
+                                                     unsigned f2, uint64_t& g_out,
+                                                     unsigned& inserted, unsigned& retries) {
+  const uint64_t b2 = t.dual ? second_bucket(t, key) : b1;
+  const int c1 = free_count(f1), c2 = b2 != b1 ? free_count(f2) : 0;
+  if (c1 == 0 && c2 == 0) return 2;
+  const bool first = c1 >= c2;
+  const uint64_t b = first ? b1 : b2;
+  const int slot = free_slot_of(first ? f1 : f2);
+  if (slot < 0) return 1;
+  const uint64_t g = b * kSlots + (uint64_t)slot;
+  if (atomicCAS(reinterpret_cast<unsigned long long*>(key_ptr(t, g)), kEmptyKey, kLockedKey) !=
+      kEmptyKey) {
+    retries++;
+    return 1;
+  }
+  write_claimed(t, b, g, key, h, sc);
+  g_out = g;
+  s.tstatus[e] = HKV_ST_INSERTED;
+  inserted++;
+  return 0;
+}
+
 __device__ __forceinline__ uint8_t claim_free_slot(const TableDev& t, const Scratch& s, uint32_t e,
                                                    uint64_t key, uint64_t h, uint64_t sc,
                                                    uint64_t& g_out, unsigned& sectors,
@@ -417,10 +459,7 @@ __device__ __forceinline__ uint8_t claim_free_slot(const TableDev& t, const Scra
       retries++;
       continue;
     }
-    atomicAdd(t.sizes + b, 1u);
-    t.digests[g] = (uint8_t)digest_from_hash(h);
-    __stcg(reinterpret_cast<unsigned long long*>(score_ptr(t, g)), (unsigned long long)sc);
-    __stcg(reinterpret_cast<unsigned long long*>(key_ptr(t, g)), (unsigned long long)key);
+    write_claimed(t, b, g, key, h, sc);
     g_out = g;
     s.tstatus[e] = HKV_ST_INSERTED;
     inserted++;
@@ -507,16 +546,20 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
     const uint64_t h = fmix64(key);
     uint64_t b = h & t.bucket_mask;
     const uint32_t pat4 = digest_from_hash(h) * 0x01010101u;
-    int slot = probe_bucket<G, false, true>(t, b, key, pat4, active, lane_g, group_bits,
-                                            group_base, kreads);
+    // upsert: the probes also report each candidate's free slots
+    const unsigned pick = (unsigned)(h >> 40);
+    unsigned f1 = 0, f2 = 0;
+    int slot = probe_bucket<G, false, true, UPSERT>(t, b, key, pat4, active, lane_g, group_bits,
+                                                    group_base, kreads, pick, &f1);
     lines += active && lane_g == 0;
     if (t.dual) {
       const uint64_t b2 = second_bucket(t, key);
       const bool need = active && slot < 0 && b2 != b;
       lines += need && lane_g == 0;
       if (__any_sync(kFull, need)) {
-        const int s2 = probe_bucket<G, false, true>(t, b2, key, pat4, need, lane_g, group_bits,
-                                                    group_base, kreads);
+        const int s2 = probe_bucket<G, false, true, UPSERT>(t, b2, key, pat4, need, lane_g,
+                                                            group_bits, group_base, kreads,
+                                                            pick, &f2);
         if (need && s2 >= 0) {
           slot = s2;
           b = b2;
@@ -550,7 +593,10 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
         } else if (!hit) {
           const uint64_t sc = policy_score(t.policy, false, 0, m, scores_in != nullptr,
                                            scores_in ? __ldg(scores_in + i) : 0, ctx);
-          flag = claim_free_slot(t, s, e, key, h, sc, gclaim, ins_lines, inserted, retries);
+          // a miss: b is still its first bucket
+          flag = claim_probed_slot(t, s, e, key, h, sc, b, f1, f2, gclaim, inserted, retries);
+          if (flag == 1)
+            flag = claim_free_slot(t, s, e, key, h, sc, gclaim, ins_lines, inserted, retries);
         }
         s.mflag[u] = flag;
         if (flag) {
