@@ -1108,6 +1108,8 @@ def run_tiered(args):
         t.insert_or_assign(keys[i], vals[i], status_out=st)
         ev[i][2].record()
 
+    if args.find_tpk or args.update_tpk:
+        t.set_launch(args.find_tpk, args.update_tpk)
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
@@ -1123,6 +1125,33 @@ def run_tiered(args):
     f_ms = sum(ev[i][0].elapsed_time(ev[i][1]) for i in range(args.warmup, nbat))
     u_ms = sum(ev[i][1].elapsed_time(ev[i][2]) for i in range(args.warmup, nbat))
     attempted = c["inserted"] + c["evicted"] + c["rejected"]
+    # find* (value-row addresses, no copy: the paper's hybrid headline) and
+    # find* followed by a gather of the rows, over the same batches on the
+    # final state
+    ptrs = torch.empty(batch, dtype=torch.int64, device=dev)
+    fp = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t.find_ptr(keys[0], ptrs, found)
+    fp[0].record()
+    for i in range(args.warmup, nbat):
+        t.find_ptr(keys[i], ptrs, found)
+    fp[1].record()
+    for i in range(args.warmup, nbat):
+        t.find_ptr(keys[i], ptrs, found)
+        hkv.gather_rows(ptrs, dim, out)
+    fp[2].record()
+    fp[2].synchronize()
+    find_ptr_bkvs = args.steps * batch / fp[0].elapsed_time(fp[1]) / 1e6
+    find_ptr_gather_bkvs = args.steps * batch / fp[1].elapsed_time(fp[2]) / 1e6
+    # device time per kernel kind over the same steps, repeated with the
+    # library's kernel events (the timed pass above has none)
+    t.sync()
+    t.profile_read()
+    t.profile_enable(True)
+    for i in range(args.warmup, nbat):
+        step(i)
+    t.profile_enable(False)
+    t.sync()
+    kernel_ms = {k: round(v[0] / args.steps, 3) for k, v in t.profile_read().items()}
     # host link reference: pinned host -> device copy bandwidth (copy engine)
     h = torch.empty(1 << 28, dtype=torch.uint8).pin_memory()
     d = torch.empty(1 << 28, dtype=torch.uint8, device=dev)
@@ -1148,6 +1177,11 @@ def run_tiered(args):
                       "lambda_fill": round(lam, 4)},
            "find_bkvs": round(args.steps * batch / f_ms / 1e6, 4),
            "upsert_bkvs": round(args.steps * batch / u_ms / 1e6, 4),
+           "find_ptr_bkvs": round(find_ptr_bkvs, 4),
+           "find_ptr_gather_bkvs": round(find_ptr_gather_bkvs, 4),
+           "kernel_ms_per_step": kernel_ms,
+           "launch": {"find_tpk": args.find_tpk or "default",
+                      "update_tpk": args.update_tpk or "default"},
            "find_hit_rate": round(c["find_hit"] / max(1, c["find_hit"] + c["find_miss"]), 4),
            "eviction_rate": round(c["evicted"] / max(1, attempted), 4),
            "rejection_rate": round(c["rejected"] / max(1, attempted), 4),

@@ -34,6 +34,14 @@ constexpr uint64_t kLockedKey = ~0ull - 1;
 constexpr uint64_t kFirstReserved = 1ull << 63;
 constexpr uint64_t kH2Salt = 0x9E3779B97F4A7C15ull;  // second-hash salt (dual mode)
 constexpr int kMaxClaimAttempts = 4096;             // bound on slot-claim retries
+constexpr uint64_t kNoHostSlot = ~0ull;             // "no host row" in host-row lists
+
+// A list of item indices grouped by the 2 MiB host region of their slots
+// (region_sort): order[0 .. *count).
+struct RegionOrder {
+  uint32_t* order;
+  unsigned long long* count;
+};
 
 struct TableDev {
   uint8_t* digests;

@@ -8,6 +8,12 @@
 // the hit through one warp ballot. The hit's value row is then copied by the
 // same G lanes with 16-byte loads and streaming stores. Dual-bucket tables
 // read the second line only when the first bucket missed.
+//
+// Tables with value slices in host memory (HOST): a hit whose row lives in
+// host memory is not copied by the probe; its slot goes to a per-key list,
+// which is grouped by host region and copied in that order afterwards
+// (hkv_hostrows.cu), since scattered host rows are bound by the device's
+// address translation.
 #include <algorithm>
 
 #include "hkv_internal.h"
@@ -17,12 +23,13 @@ namespace {
 
 constexpr int kFindThreads = 256;
 
-template <int G, bool VEC16, bool VALUES>
+template <int G, bool VEC16, bool VALUES, bool HOST = false>
 __global__ void __launch_bounds__(kFindThreads, 8)
     find_kernel(TableDev t, uint64_t n, const uint64_t* __restrict__ keys,
                 float* __restrict__ out, uint8_t* __restrict__ found,
                 uint64_t* __restrict__ scores_out, const OpDesc* __restrict__ d,
-                const float** __restrict__ ptrs_out) {
+                const float** __restrict__ ptrs_out, uint64_t* __restrict__ hslot = nullptr,
+                uint64_t host0 = 0) {
   if (d) {
     n = d->n;
     keys = d->keys;
@@ -63,11 +70,14 @@ __global__ void __launch_bounds__(kFindThreads, 8)
       }
     }
     const bool hit = active && slot >= 0;
+    const uint64_t g = b * kSlots + (uint64_t)slot;
+    const bool later = HOST && hit && g >= host0;  // a host row: copied in region order
     if (hit) {
-      const uint64_t g = b * kSlots + (uint64_t)slot;
-      if (VALUES) copy_row<G, VEC16, true>(out + i * t.dim, value_ptr(t, g), t.dim, lane_g);
+      if (VALUES && !later)
+        copy_row<G, VEC16, true>(out + i * t.dim, value_ptr(t, g), t.dim, lane_g);
       if (scores_out && lane_g == 0) scores_out[i] = __ldg(score_ptr(t, g));
     }
+    if (HOST && in && lane_g == 0) hslot[i] = later ? g : kNoHostSlot;
     if (in && lane_g == 0) {
       if (found) found[i] = hit ? 1 : 0;
       if (ptrs_out) ptrs_out[i] = hit ? value_ptr(t, b * kSlots + (uint64_t)slot) : nullptr;
@@ -83,22 +93,30 @@ __global__ void __launch_bounds__(kFindThreads, 8)
 template <int G>
 void launch_g(const hkv_table_s* t, uint64_t n, const uint64_t* keys, float* out, uint8_t* found,
               uint64_t* scores_out, bool vec16, cudaStream_t s, const OpDesc* d = nullptr,
-              bool values_if_desc = false, const float** ptrs = nullptr) {
+              bool values_if_desc = false, const float** ptrs = nullptr,
+              uint64_t* hslot = nullptr) {
   const bool values = d ? values_if_desc : out != nullptr;
   uint64_t warps_needed = (n + (32 / G) - 1) / (32 / G);
   uint64_t blocks = (warps_needed * 32 + kFindThreads - 1) / kFindThreads;
   uint64_t cap = (uint64_t)t->num_sms * (2048 / kFindThreads);
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
-  if (!values)
+  if (hslot)  // values with host rows listed (vec16 only)
+    launch_table_kernel(t, find_kernel<G, true, true, true>, (unsigned)blocks, kFindThreads, 0,
+                        s, t->dev, n, keys, out, found, scores_out, d, ptrs, hslot,
+                        t->hbm_value_slots);
+  else if (!values)
     launch_table_kernel(t, find_kernel<G, false, false>, (unsigned)blocks, kFindThreads, 0, s,
-                        t->dev, n, keys, out, found, scores_out, d, ptrs);
+                        t->dev, n, keys, out, found, scores_out, d, ptrs, nullptr,
+                        (uint64_t)0);
   else if (vec16)
     launch_table_kernel(t, find_kernel<G, true, true>, (unsigned)blocks, kFindThreads, 0, s,
-                        t->dev, n, keys, out, found, scores_out, d, ptrs);
+                        t->dev, n, keys, out, found, scores_out, d, ptrs, nullptr,
+                        (uint64_t)0);
   else
     launch_table_kernel(t, find_kernel<G, false, true>, (unsigned)blocks, kFindThreads, 0, s,
-                        t->dev, n, keys, out, found, scores_out, d, ptrs);
+                        t->dev, n, keys, out, found, scores_out, d, ptrs, nullptr,
+                        (uint64_t)0);
 }
 
 }  // namespace
@@ -108,13 +126,34 @@ hkv_status launch_find(hkv_table_s* t, uint64_t n, const uint64_t* keys, float* 
   if (n == 0) return HKV_OK;
   KernelTimer timer(t->prof, HKV_K_FIND, s);
   bool vec16 = (t->dev.dim % 4 == 0) && ((reinterpret_cast<uintptr_t>(values_out) & 15) == 0);
+  // host rows of a tiered table: listed by the probe, copied in region order
+  void* scratch = nullptr;
+  uint64_t* hslot = nullptr;
+  if (values_out && vec16 && !t->host_slices.empty()) {
+    const uint64_t hb = (n * 8 + 255) & ~255ull;
+    if (cudaMallocFromPoolAsync(&scratch, hb + region_sort_bytes(t, n), t->pool, s) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      set_last_error("find scratch allocation failed");
+      return HKV_ERR_OOM;
+    }
+    hslot = static_cast<uint64_t*>(scratch);
+  }
   switch (t->launch.find_tpk) {
-    case 1: launch_g<1>(t, n, keys, values_out, found, scores_out, vec16, s); break;
-    case 2: launch_g<2>(t, n, keys, values_out, found, scores_out, vec16, s); break;
-    case 4: launch_g<4>(t, n, keys, values_out, found, scores_out, vec16, s); break;
-    case 16: launch_g<16>(t, n, keys, values_out, found, scores_out, vec16, s); break;
-    case 32: launch_g<32>(t, n, keys, values_out, found, scores_out, vec16, s); break;
-    default: launch_g<8>(t, n, keys, values_out, found, scores_out, vec16, s); break;
+    case 1: launch_g<1>(t, n, keys, values_out, found, scores_out, vec16, s, nullptr, false, nullptr, hslot); break;
+    case 2: launch_g<2>(t, n, keys, values_out, found, scores_out, vec16, s, nullptr, false, nullptr, hslot); break;
+    case 4: launch_g<4>(t, n, keys, values_out, found, scores_out, vec16, s, nullptr, false, nullptr, hslot); break;
+    case 16: launch_g<16>(t, n, keys, values_out, found, scores_out, vec16, s, nullptr, false, nullptr, hslot); break;
+    case 32: launch_g<32>(t, n, keys, values_out, found, scores_out, vec16, s, nullptr, false, nullptr, hslot); break;
+    default: launch_g<8>(t, n, keys, values_out, found, scores_out, vec16, s, nullptr, false, nullptr, hslot); break;
+  }
+  if (hslot) {
+    RegionOrder ro;
+    const uint64_t hb = (n * 8 + 255) & ~255ull;
+    hkv_status rc = region_sort(t, hslot, n, nullptr, static_cast<char*>(scratch) + hb, &ro, s);
+    if (rc == HKV_OK) rc = launch_host_rows_gather(t, n, hslot, ro, values_out, true, s);
+    cudaFreeAsync(scratch, s);
+    if (rc) return rc;
   }
   return cuda_status(cudaGetLastError(), "find launch");
 }

@@ -114,6 +114,11 @@ struct hkv_table_s {
   void* meta = nullptr;                 // digests + keys + scores + err + counters
   std::vector<void*> hbm_slices;
   std::vector<void*> host_slices;
+  // The host slices, when they were carved from one mapping registered with
+  // CUDA (huge-page advised) rather than allocated one by one.
+  void* host_map = nullptr;
+  uint64_t host_map_bytes = 0;
+  void* host_base = nullptr;            // first host slice inside host_map
   float** slices_dev = nullptr;
   cudaMemPool_t pool = nullptr;         // stream-ordered scratch allocations
   hkv::TripleGroup<hkv::CudaEvents> sched;
@@ -194,6 +199,18 @@ hkv_status launch_upsert_in(hkv_table_s* t, uint64_t n, const uint64_t* keys, co
                             const uint64_t* scores, uint8_t* status_out, uint64_t* ev_keys,
                             uint64_t* ev_scores, uint64_t* n_evicted, ScoreCtx ctx,
                             void* scratch, uint64_t scratch_bytes, cudaStream_t s);
+// Host-memory value rows in address order (tiered tables, hkv_hostrows.cu).
+// region_sort groups the items j < m (m = *m_dev when given, else m_max)
+// with slot[j] != kNoHostSlot, all of them slots in host memory, by 2 MiB
+// region; scratch is region_sort_bytes(t, m_max) bytes of device memory.
+uint64_t region_sort_bytes(const hkv_table_s* t, uint64_t m_max);
+hkv_status region_sort(const hkv_table_s* t, const uint64_t* slot, uint64_t m_max,
+                       const unsigned long long* m_dev, void* scratch, RegionOrder* out,
+                       cudaStream_t st);
+// out[i] = the row of slot hslot[i] for every listed i (find with values).
+hkv_status launch_host_rows_gather(const hkv_table_s* t, uint64_t n, const uint64_t* hslot,
+                                   const RegionOrder& ro, float* out, bool vec16,
+                                   cudaStream_t st);
 // Batched rounds: size, buffers and score context come from a device
 // OpDesc; grids are sized for n_max, scratch is the caller's block of
 // upsert_scratch_bytes(n_max) bytes. No allocation, no profiling events.

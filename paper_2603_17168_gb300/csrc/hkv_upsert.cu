@@ -79,7 +79,13 @@ struct Scratch {
   int keep_hits;             // find_or_insert: residents keep their values
   int row_prefetch;          // input rows are in device memory: the insert
                              // phase may pull them into L2 by bulk prefetch
+  uint64_t* gdefer;          // [n] phase I: host-memory slot taken by distinct
+                             // key u whose row is written after the phase
+                             // (kNoSlotDefer if none), or null: rows now
+  uint64_t host_slot0;       // first global slot whose row lives in host memory
 };
+
+constexpr uint64_t kNoSlotDefer = kNoHostSlot;
 
 __device__ __forceinline__ uint64_t dedup_pos(uint64_t key, int bits) {
   // top bits of a hash independent of the table's bucket bits
@@ -571,8 +577,15 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
     if (active) {
       if (hit) {
         const uint64_t g = b * kSlots + (uint64_t)slot;
-        if (values && !s.keep_hits)
+        if (UPSERT && s.gdefer && !s.evv && g >= s.host_slot0) {
+          // a host-memory row: written later, in region order
+          if (lane_g == 0) {
+            s.gdefer[u] = g;
+            s.mi[u] = (uint32_t)i;
+          }
+        } else if (values && !s.keep_hits) {
           copy_row<G, VEC16, false>(value_ptr(t, g), values + i * t.dim, t.dim, lane_g);
+        }
         if (lane_g == 0) {
           update_resident_score(t, g, m, scores_in != nullptr, scores_in ? __ldg(scores_in + i) : 0,
                                 ctx);
@@ -607,9 +620,19 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
       }
     }
     if (UPSERT) {
-      // the row of a slot claimed above, copied by the key's G lanes
+      // the row of a slot claimed above, copied by the key's G lanes (a
+      // host-memory row later, in region order)
       const uint64_t gc = __shfl_sync(kFull, gclaim, group_base);
-      if (gc != kNoSlot) copy_row<G, VEC16, false>(value_ptr(t, gc), values + i * t.dim, t.dim, lane_g);
+      if (gc != kNoSlot) {
+        if (s.gdefer && !s.evv && gc >= s.host_slot0) {
+          if (lane_g == 0) {
+            s.gdefer[u] = gc;
+            s.mi[u] = (uint32_t)i;
+          }
+        } else {
+          copy_row<G, VEC16, false>(value_ptr(t, gc), values + i * t.dim, t.dim, lane_g);
+        }
+      }
     }
   }
   const int which[7] = {HKV_CNT_UPDATED, HKV_CNT_UPD_LINES, HKV_CNT_UPD_KEYS, HKV_CNT_INSERTED,
@@ -662,15 +685,21 @@ __device__ __forceinline__ int held_slot(int lane, int q) {
 // memory; the lanes' value stores are ordered before the key by the warp
 // barrier and the release, so no later writer of the slot can be overtaken
 // by them.
+//
+// With `row` false the value row is left to the deferred-row pass (a slot
+// in host memory, see flush_deferred_rows_kernel): the release then waits
+// on nothing slower than the HBM stores of the digest and score.
 template <bool VEC16>
 __device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_t key, uint64_t sc,
-                                          uint32_t dg, const float* src, int lane) {
+                                          uint32_t dg, const float* src, int lane,
+                                          bool row = true) {
   if (lane == 0) {
     t.digests[g] = (uint8_t)dg;
     __stcg(reinterpret_cast<unsigned long long*>(score_ptr(t, g)), (unsigned long long)sc);
   }
   float* dst = value_ptr(t, g);
-  if (VEC16) {
+  if (!row) {
+  } else if (VEC16) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
     float4* d4 = reinterpret_cast<float4*>(dst);
     for (uint32_t j = lane; j < (t.dim >> 2); j += 32) __stcg(d4 + j, __ldg(s4 + j));
@@ -868,7 +897,10 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
           const float* vsrc = value_ptr(t, g);
           for (uint32_t d = lane; d < t.dim; d += 32) s.evv[u * t.dim + d] = __ldcg(vsrc + d);
         }
-        fill_slot<VEC16>(t, g, key, sc, dg, src, lane);
+        // a row bound for host memory waits for the deferred-row pass
+        const bool defer = s.gdefer != nullptr && g >= s.host_slot0;
+        if (defer && lane == 0) s.gdefer[u] = g;
+        fill_slot<VEC16>(t, g, key, sc, dg, src, lane, !defer);
         victim_key = kmin;
         outcome = HKV_ST_INSERTED;
         evicted++;
@@ -1172,6 +1204,37 @@ __global__ void __launch_bounds__(kRecThreads)
 
 constexpr int kStatusPerThread = 4;  // positions a thread has in flight per round
 
+// Deferred rows (tables with host-memory slices). A slot in host memory
+// that phase U updated or claimed, or that phase I replaced, got its key,
+// score and digest in its phase but not its value row: phase U would have
+// scattered rows over the whole host range, and phase I would have waited
+// for each row to cross the host link before publishing the key. The
+// distinct keys that own such slots are grouped by host region
+// (region_sort) and each writes its row here, in that order, if its slot
+// still holds it (a slot replaced again later in the batch belongs to the
+// later key, whose own entry writes it). Phase U keeps its rows direct when
+// evicted values are asked for, so that a victim's reported row is its
+// value after phase U. Groups of 8 lanes per row keep many rows in flight.
+constexpr int kFlushThreads = 256;
+constexpr int kFlushLanes = 8;
+
+template <bool VEC16>
+__global__ void __launch_bounds__(kFlushThreads)
+    flush_deferred_rows_kernel(TableDev t, Scratch s, RegionOrder ro,
+                               const float* __restrict__ values) {
+  const uint64_t m = *ro.count;
+  const int lane_g = threadIdx.x & (kFlushLanes - 1);
+  const uint64_t grp = (blockIdx.x * (uint64_t)kFlushThreads + threadIdx.x) / kFlushLanes;
+  const uint64_t ngrp = (uint64_t)gridDim.x * kFlushThreads / kFlushLanes;
+  for (uint64_t p = grp; p < m; p += ngrp) {
+    const uint64_t u = ro.order[p];
+    const uint64_t g = s.gdefer[u];
+    if (__ldcg(reinterpret_cast<const unsigned long long*>(key_ptr(t, g))) != s.mkey[u]) continue;
+    copy_row<kFlushLanes, VEC16, false>(value_ptr(t, g), values + (uint64_t)s.mi[u] * t.dim,
+                                        t.dim, lane_g);
+  }
+}
+
 __global__ void status_kernel(uint64_t n, Scratch s, uint8_t* __restrict__ status_out,
                               uint64_t* __restrict__ n_evicted) {
   if (aborted(s)) return;
@@ -1260,6 +1323,7 @@ __global__ void __launch_bounds__(kUpdThreads)
 struct ScratchAlloc {
   Scratch s{};
   void* base = nullptr;
+  void* region = nullptr;  // region_sort scratch of the deferred rows, or null
 };
 
 uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
@@ -1279,8 +1343,11 @@ hkv_status alloc_scratch(hkv_table_s* t, uint64_t n, bool upsert, bool want_ev_v
   // deterministic dual-bucket upserts run phase I in ordered waves
   const bool ordered = upsert && t->opts.deterministic && t->dev.dual;
   const uint64_t sz_owner = ordered ? align256(t->num_buckets * 8) : 0;
+  // phase I defers the rows of host-memory slots (tiered tables)
+  const bool defer = upsert && !ordered && !t->host_slices.empty();
+  const uint64_t sz_defer = defer ? sz_u64 + align256(region_sort_bytes(t, n)) : 0;
   uint64_t total = sz_tab + sz_ts + 2 * sz_u32 + sz_cnt + sz_u64;
-  if (upsert) total += sz_u8 + 2 * sz_u64 + 2 * sz_u32 + sz_evv + sz_owner;
+  if (upsert) total += sz_u8 + 2 * sz_u64 + 2 * sz_u32 + sz_evv + sz_owner + sz_defer;
   cudaError_t e = cudaMallocFromPoolAsync(&a->base, total, t->pool, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1306,7 +1373,12 @@ hkv_status alloc_scratch(hkv_table_s* t, uint64_t n, bool upsert, bool want_ev_v
     s.evv = want_ev_values ? reinterpret_cast<float*>(p) : nullptr;
     p += sz_evv;
     s.owner = ordered ? reinterpret_cast<unsigned long long*>(p) : nullptr;
+    p += sz_owner;
     if (ordered) cudaMemsetAsync(s.owner, 0, t->num_buckets * 8, st);
+    s.gdefer = defer ? reinterpret_cast<uint64_t*>(p) : nullptr;
+    a->region = defer ? p + sz_u64 : nullptr;
+    s.host_slot0 = t->hbm_value_slots;
+    if (defer) cudaMemsetAsync(s.gdefer, 0xFF, n * 8, st);
   }
   cudaMemsetAsync(s.tab, 0xFF, T * sizeof(DedupEntry), st);
   cudaMemsetAsync(s.cnt, 0, kCntWords * 8, st);
@@ -1444,6 +1516,19 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
     else
       launch_table_kernel(t, insert_kernel<false>, ig, kInsThreads, 0, st, t->dev, s, values,
                           scores, ctx);
+    if (s.gdefer) {
+      RegionOrder ro;
+      rc = region_sort(t, s.gdefer, n, s.cnt + kCntUnique, a.region, &ro, st);
+      if (rc) {
+        cudaFreeAsync(a.base, st);
+        return rc;
+      }
+      const unsigned fg = grid_for(t, n * kFlushLanes, kFlushThreads, 8);
+      if (vec16)
+        flush_deferred_rows_kernel<true><<<fg, kFlushThreads, 0, st>>>(t->dev, s, ro, values);
+      else
+        flush_deferred_rows_kernel<false><<<fg, kFlushThreads, 0, st>>>(t->dev, s, ro, values);
+    }
   }
   {
     KernelTimer timer(t->prof, HKV_K_RECONCILE, st);

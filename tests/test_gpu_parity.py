@@ -332,9 +332,12 @@ def test_dual_bucket_invariants_count_and_find():
         compare_find(t, ref, q)
 
 
-def test_tiered_values_in_host_memory():
+@pytest.mark.parametrize("evicted_values", [True, False])
+def test_tiered_values_in_host_memory(evicted_values):
     """Values past a small HBM budget live in pinned mapped host slices; the
-    results are the same bit for bit."""
+    results are the same bit for bit. Host-memory rows are written after the
+    probes, grouped by host region (phase I always; phase U too when no
+    evicted values are asked for), and find copies host rows the same way."""
     rng = np.random.default_rng(1400)
     nb, dim = 128, 16
     slice_bytes = 8 * 128 * dim * 4                       # 8 buckets per slice
@@ -345,9 +348,52 @@ def test_tiered_values_in_host_memory():
     z = w.Zipf(0.99, 1 << 20)
     for _ in range(6):
         keys = z.keys(rng, 8000)
-        compare_upsert(t, o, keys, w.normal_values(rng, keys.size, dim))
+        vals = w.normal_values(rng, keys.size, dim)
+        if evicted_values:
+            compare_upsert(t, o, keys, vals)
+        else:
+            ost, oek, oes, _ = o.insert_or_assign(keys, vals)
+            gst, gek, ges, _ = gpu_upsert(t, keys, vals, want_values=False)
+            assert np.array_equal(gst, ost), "statuses differ"
+            o_ord = np.argsort(oek, kind="stable")
+            assert np.array_equal(gek, oek[o_ord]) and np.array_equal(ges, oes[o_ord])
+        compare_find(t, o, z.keys(rng, 6000))
     same_state(export_state(t), o.export())
     compare_find(t, o, z.keys(rng, 10000))
+
+
+def test_tiered_dual_bucket_invariants_and_last_value():
+    """A dual-bucket table with most value rows in host memory, driven past
+    lambda 1 with Zipf batches: phase I writes the rows of host-memory slots
+    after the victim searches. The invariants hold, the size stays within
+    0.1% of the oracle's, every resident key holds the last value written to
+    it, and find on the GPU's own state matches the oracle loaded with it."""
+    rng = np.random.default_rng(1450)
+    nb, dim = 256, 32
+    slice_bytes = 16 * 128 * dim * 4                      # 16 buckets per slice
+    t = hkv.Table(nb * 128, dim, hkv.LFU, dual_bucket=True,
+                  hbm_value_budget_bytes=3 * slice_bytes, slice_bytes=slice_bytes)
+    assert t.hbm_value_slots == 3 * 16 * 128
+    o = oracle.OracleTable(nb, dim, oracle.LFU, True)
+    z = w.Zipf(1.05, 1 << 20)
+    last = {}
+    for b in range(10):
+        # uniform keys past the capacity, then Zipf batches at lambda 1
+        keys = w.uniform_keys(rng, 9000) if b < 6 else z.keys(rng, 12000)
+        vals = w.normal_values(rng, keys.size, dim)
+        # no evicted values asked for: phase U defers its host rows too
+        gst, gek, ges, _ = gpu_upsert(t, keys, vals, want_values=False)
+        o.insert_or_assign(keys, vals)
+        for k, v in zip(keys.tolist(), vals):
+            last[k] = v
+        gk, gs, gv, gb = _check_batch_invariants(t, nb, keys, gst, gek, ges)
+        assert abs(t.size() - o.size()) <= 0.001 * o.size()
+    assert t.size() > 0.99 * t.capacity
+    for k, v in zip(gk.tolist(), gv):
+        assert v.tobytes() == last[k].tobytes(), "a resident key lost its last value"
+    ref = oracle.OracleTable(nb, dim, oracle.LFU, True)
+    ref.load(gk, gs, gv, gb)
+    compare_find(t, ref, np.concatenate([z.keys(rng, 8000), w.uniform_keys(rng, 4000)]))
 
 
 def test_streams_follow_the_triple_group_order():
