@@ -83,6 +83,10 @@ def parse_args(argv=None):
     p.add_argument("--serve-pool", type=int, default=512)
     p.add_argument("--serve-peak-requests", type=int, default=4096)
     p.add_argument("--serve-seconds", type=float, default=3.0)
+    p.add_argument("--no-served", action="store_true",
+                   help="single-table workload: skip the short serving-loop record")
+    p.add_argument("--served-seconds", type=float, default=2.0,
+                   help="seconds per offered load of the serving record in the default run")
     p.add_argument("--multi-lambda", type=float, default=1.0)
     p.add_argument("--multi-shrink", type=int, default=0,
                    help="divide the multi-table slot counts by 2^k (small runs)")
@@ -1114,6 +1118,11 @@ def run_tiered(args):
         step(i)
     torch.cuda.synchronize()
     t.reset_counters()
+    # the library's kernel events stay on in the timed pass: a step takes
+    # milliseconds, against microseconds of event recording
+    t.sync()
+    t.profile_read()
+    t.profile_enable(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for i in range(args.warmup, nbat):
@@ -1121,6 +1130,9 @@ def run_tiered(args):
     e1.record()
     e1.synchronize()
     ms = e0.elapsed_time(e1)
+    t.profile_enable(False)
+    t.sync()
+    kernel_ms = {k: round(v[0] / args.steps, 3) for k, v in t.profile_read().items()}
     c = t.read_counters()
     f_ms = sum(ev[i][0].elapsed_time(ev[i][1]) for i in range(args.warmup, nbat))
     u_ms = sum(ev[i][1].elapsed_time(ev[i][2]) for i in range(args.warmup, nbat))
@@ -1142,16 +1154,7 @@ def run_tiered(args):
     fp[2].synchronize()
     find_ptr_bkvs = args.steps * batch / fp[0].elapsed_time(fp[1]) / 1e6
     find_ptr_gather_bkvs = args.steps * batch / fp[1].elapsed_time(fp[2]) / 1e6
-    # device time per kernel kind over the same steps, repeated with the
-    # library's kernel events (the timed pass above has none)
-    t.sync()
-    t.profile_read()
-    t.profile_enable(True)
-    for i in range(args.warmup, nbat):
-        step(i)
-    t.profile_enable(False)
-    t.sync()
-    kernel_ms = {k: round(v[0] / args.steps, 3) for k, v in t.profile_read().items()}
+
     # host link reference: pinned host -> device copy bandwidth (copy engine)
     h = torch.empty(1 << 28, dtype=torch.uint8).pin_memory()
     d = torch.empty(1 << 28, dtype=torch.uint8, device=dev)
@@ -1207,6 +1210,8 @@ def _latency_stats(items, res, stats=None):
     keys = sum(int(it["keys"].numel()) for it in items)
     out = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
            "p99_ms": round(float(np.percentile(lat, 99)), 3),
+           "p999_ms": round(float(np.percentile(lat, 99.9)), 3),
+           "max_ms": round(float(lat.max()), 3),
            "bkvs": round(keys / span / 1e9, 4), "requests": len(items),
            "rounds": len({r.round for r in res})}
     if stats:
@@ -1366,6 +1371,26 @@ def run_serve(args):
                        "link_bound_bkvs": round(link_bound, 4),
                        "step": "a request; value = closed-loop peak of the batched loop"},
             "peak": {"batched": peak_b, "plain": peak_p}, "served": served}
+
+
+def served_record(args):
+    """The serving workload's latency half of the metric in the default run:
+    the same server, tables and request pool as --workload serve, with
+    args.served_seconds per offered load (the full record uses 60 s)."""
+    import copy
+    a = copy.copy(args)
+    a.serve_seconds = args.served_seconds
+    r = run_serve(a)
+    keep = ("p50_ms", "p99_ms", "bkvs", "requests")
+    return {"workload": r["config"]["workload"],
+            "seconds_per_load": a.serve_seconds,
+            "link_bound_bkvs": r["config"]["link_bound_bkvs"],
+            "peak_bkvs": {"batched": r["peak"]["batched"]["bkvs"],
+                          "plain": r["peak"]["plain"]["bkvs"]},
+            "loads": {k: {"offered_bkvs": v["offered_bkvs"],
+                          "batched": {x: v["batched"][x] for x in keep},
+                          "plain": {x: v["plain"][x] for x in keep}}
+                      for k, v in r["served"].items()}}
 
 
 def distinct_keys_torch(gen, n, universe, dev):
@@ -1667,6 +1692,8 @@ def main(argv=None):
         rank, world, _ = dist_env()
         if res is not None and rank == 0:
             res["cpu_baseline"] = None if (args.no_cpu_baseline or world > 1) else cpu_baseline()
+            if not args.no_served and world == 1:
+                res["served"] = served_record(args)
     if res is not None:
         print(json.dumps(res), flush=True)
     rank, world, _ = dist_env()

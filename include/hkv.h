@@ -321,6 +321,14 @@ hkv_status hkv_reset_counters(hkv_table_t t, hkv_stream_t stream);
  * these; defaults follow the value width. */
 hkv_status hkv_set_launch(hkv_table_t t, int find_threads_per_key, int update_threads_per_key);
 
+/* Widest vector the value-row copies of find, the update phase and the
+ * insert phase use: 16, 8 or 4 bytes (0 restores the default, 16). A call
+ * whose row addresses do not allow it (16 bytes: dim % 4 == 0 and 16-byte
+ * aligned rows; 8 bytes: dim even and 8-byte aligned rows) takes the widest
+ * width they allow below it. Results do not depend on it. The autotuner
+ * sets it with the threads per key. */
+hkv_status hkv_set_value_vector(hkv_table_t t, int bytes);
+
 /* Concurrency rule between calls on different streams (Sec. 3.5, Table 4).
  * HKV_CC_TRIPLE_GROUP (default): readers run beside readers and updaters
  * beside updaters, every other pair is ordered. HKV_CC_RW_LOCK: the

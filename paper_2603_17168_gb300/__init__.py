@@ -86,6 +86,7 @@ SIGNATURES = {
     "hkv_read_counters": (_i32, [_vp, _P64, _vp]),
     "hkv_reset_counters": (_i32, [_vp, _vp]),
     "hkv_set_launch": (_i32, [_vp, _i32, _i32]),
+    "hkv_set_value_vector": (_i32, [_vp, _i32]),
     "hkv_find_ptr": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp]),
     "hkv_find_or_insert": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp, _vp]),
     "hkv_gather_rows": (_i32, [_vp, _u64, _u32, _vp, _vp]),
@@ -394,6 +395,11 @@ class Table:
     def set_launch(self, find_threads_per_key: int = 0, update_threads_per_key: int = 0):
         _check(load_library().hkv_set_launch(self._h, find_threads_per_key,
                                              update_threads_per_key))
+
+    def set_value_vector(self, nbytes: int = 0):
+        """Widest vector (16, 8 or 4 bytes; 0: default 16) of the value-row
+        copies (hkv_set_value_vector)."""
+        _check(load_library().hkv_set_value_vector(self._h, int(nbytes)))
 
     def set_concurrency(self, rw_lock: bool):
         """Triple-group rule (default) or a reader/writer lock (Exp 3e)."""

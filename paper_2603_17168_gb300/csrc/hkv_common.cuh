@@ -54,6 +54,7 @@ struct TableDev {
   uint32_t slice_shift;      // log2(slots per slice)
   int32_t policy;
   int32_t dual;
+  int32_t vec8;              // copies without 16-byte vectors use 8-byte ones
   uint32_t* err;             // latched device error (first error wins)
   unsigned long long* counters;  // [HKV_COUNTER_COUNT]
 };
@@ -403,12 +404,14 @@ __device__ __forceinline__ int probe_bucket(const TableDev& t, uint64_t b, uint6
 }
 
 // Copy one value row of `dim` floats with G cooperating lanes, using 16-byte
-// vectors when VEC16 (dim % 4 == 0 and 16-byte aligned rows), else 4-byte.
-// Each lane issues R loads before it stores them, so a row costs one memory
-// latency per R vectors per lane rather than one per vector (rows in mapped
-// host memory are a link round trip away).
+// vectors when VEC16 (dim % 4 == 0 and 16-byte aligned rows), else 8-byte
+// vectors when vec8 (set by the launcher for even dim and 8-byte aligned
+// rows), else 4-byte words. Each lane issues R loads before it stores them,
+// so a row costs one memory latency per R vectors per lane rather than one
+// per vector (rows in mapped host memory are a link round trip away).
 template <int G, bool VEC16, bool STREAM_DST, int R = HKV_COPY_ROW_R>
-__device__ __forceinline__ void copy_row(float* dst, const float* src, uint32_t dim, int lane_g) {
+__device__ __forceinline__ void copy_row(float* dst, const float* src, uint32_t dim, int lane_g,
+                                         bool vec8 = false) {
   if constexpr (VEC16) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
     float4* d4 = reinterpret_cast<float4*>(dst);
@@ -423,6 +426,14 @@ __device__ __forceinline__ void copy_row(float* dst, const float* src, uint32_t 
         if (j0 + r * G >= n4) break;
         if (STREAM_DST) __stcs(d4 + j0 + r * G, v[r]); else d4[j0 + r * G] = v[r];
       }
+    }
+  } else if (vec8 && (dim & 1) == 0 &&
+             ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 7) == 0) {
+    const float2* s2 = reinterpret_cast<const float2*>(src);
+    float2* d2 = reinterpret_cast<float2*>(dst);
+    for (uint32_t j = lane_g; j < (dim >> 1); j += G) {
+      float2 v = __ldg(s2 + j);
+      if (STREAM_DST) __stcs(d2 + j, v); else d2[j] = v;
     }
   } else {
     for (uint32_t j = lane_g; j < dim; j += G) {

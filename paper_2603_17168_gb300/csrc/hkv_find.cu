@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kFindThreads, 8)
     const bool later = HOST && hit && g >= host0;  // a host row: copied in region order
     if (hit) {
       if (VALUES && !later)
-        copy_row<G, VEC16, true>(out + i * t.dim, value_ptr(t, g), t.dim, lane_g);
+        copy_row<G, VEC16, true>(out + i * t.dim, value_ptr(t, g), t.dim, lane_g, t.vec8);
       if (scores_out && lane_g == 0) scores_out[i] = __ldg(score_ptr(t, g));
     }
     if (HOST && in && lane_g == 0) hslot[i] = later ? g : kNoHostSlot;
@@ -125,7 +125,7 @@ hkv_status launch_find(hkv_table_s* t, uint64_t n, const uint64_t* keys, float* 
                        uint8_t* found, uint64_t* scores_out, cudaStream_t s) {
   if (n == 0) return HKV_OK;
   KernelTimer timer(t->prof, HKV_K_FIND, s);
-  bool vec16 = (t->dev.dim % 4 == 0) && ((reinterpret_cast<uintptr_t>(values_out) & 15) == 0);
+  const bool vec16 = row_vector_bytes(t, values_out) == 16;
   // host rows of a tiered table: listed by the probe, copied in region order
   void* scratch = nullptr;
   uint64_t* hslot = nullptr;
@@ -216,7 +216,7 @@ hkv_status launch_find_desc(hkv_table_s* t, uint64_t n_max, const OpDesc* d, boo
   // Sized for n_max; the kernel reads the round's size and buffers from d,
   // whose value rows the batch object keeps 16-byte aligned.
   const uint64_t n = n_max ? n_max : 1;
-  const bool vec16 = t->dev.dim % 4 == 0;
+  const bool vec16 = row_vector_bytes(t, nullptr) == 16;  // rows checked 16-byte aligned
   switch (t->launch.find_tpk) {
     case 1: launch_g<1>(t, n, nullptr, nullptr, nullptr, nullptr, vec16, s, d, values); break;
     case 2: launch_g<2>(t, n, nullptr, nullptr, nullptr, nullptr, vec16, s, d, values); break;

@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(kSortThreads)
   const uint64_t ngrp = (uint64_t)gridDim.x * kSortThreads / kRowLanes;
   for (uint64_t p = grp; p < m; p += ngrp) {
     const uint64_t i = ro.order[p];
-    copy_row<kRowLanes, VEC16, true>(out + i * t.dim, value_ptr(t, hslot[i]), t.dim, lane_g);
+    copy_row<kRowLanes, VEC16, true>(out + i * t.dim, value_ptr(t, hslot[i]), t.dim, lane_g,
+                                     t.vec8);
   }
 }
 

@@ -95,6 +95,7 @@ class KernelTimer {
 struct LaunchCfg {
   int find_tpk = 8;    // threads per key, find / contains
   int update_tpk = 8;  // threads per key, update phase of upsert / assign
+  int vec_bytes = 16;  // widest value-row copy vector (16, 8 or 4)
 };
 
 }  // namespace hkv
@@ -160,6 +161,11 @@ void set_l2_window(hkv_table_s* t, uint64_t want);
 }  // namespace hkv
 
 namespace hkv {
+
+// Widest vector (16, 8 or 4 bytes) a value-row copy between rows of `dim`
+// floats at the given row arrays (null: not involved) may use under t's
+// vec_bytes setting; table rows are 16-byte aligned.
+int row_vector_bytes(const hkv_table_s* t, const void* a, const void* b = nullptr);
 
 void set_last_error(const std::string& msg);
 hkv_status cuda_status(cudaError_t e, const char* what);

@@ -102,6 +102,14 @@ hkv_status fail(hkv_status s, const std::string& msg) {
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
+int row_vector_bytes(const hkv_table_s* t, const void* a, const void* b) {
+  const uintptr_t m = reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b);
+  const uint32_t dim = t->dev.dim;
+  if (t->launch.vec_bytes >= 16 && dim % 4 == 0 && (m & 15) == 0) return 16;
+  if (t->launch.vec_bytes >= 8 && dim % 2 == 0 && (m & 7) == 0) return 8;
+  return 4;
+}
+
 bool in_device_memory(const void* p) {
   cudaPointerAttributes a{};
   if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -253,6 +261,7 @@ hkv_status hkv_create(const hkv_options* o, hkv_table_t* out) {
   t->dev.dim = o->dim;
   t->dev.policy = o->policy;
   t->dev.dual = o->dual_bucket ? 1 : 0;
+  t->dev.vec8 = 1;  // 8-byte copies where 16-byte ones are not possible
 
   // value slices: a power-of-two number of buckets each
   const uint64_t want_slice = o->slice_bytes ? o->slice_bytes : kDefaultSlice;
@@ -649,6 +658,15 @@ hkv_status hkv_profile_read(hkv_table_t t, double* ms_out, uint64_t* launches_ou
   }
   t->prof.recs.clear();
   return rc;
+}
+
+hkv_status hkv_set_value_vector(hkv_table_t t, int bytes) {
+  if (bad(t)) return fail(HKV_ERR_INVALID_ARG, "null table");
+  if (bytes != 0 && bytes != 4 && bytes != 8 && bytes != 16)
+    return fail(HKV_ERR_INVALID_ARG, "value vector width must be 4, 8 or 16 bytes");
+  t->launch.vec_bytes = bytes ? bytes : 16;
+  t->dev.vec8 = t->launch.vec_bytes >= 8 ? 1 : 0;
+  return HKV_OK;
 }
 
 hkv_status hkv_set_launch(hkv_table_t t, int find_tpk, int update_tpk) {

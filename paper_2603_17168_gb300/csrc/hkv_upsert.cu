@@ -365,6 +365,11 @@ __device__ __forceinline__ void fill_slot_thread(const TableDev& t, uint64_t g, 
     const float4* s4 = reinterpret_cast<const float4*>(src);
     float4* d4 = reinterpret_cast<float4*>(dst);
     for (uint32_t j = 0; j < (t.dim >> 2); ++j) __stcg(d4 + j, __ldg(s4 + j));
+  } else if (t.vec8 && (t.dim & 1) == 0 &&
+             ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 7) == 0) {
+    const float2* s2 = reinterpret_cast<const float2*>(src);
+    float2* d2 = reinterpret_cast<float2*>(dst);
+    for (uint32_t j = 0; j < (t.dim >> 1); ++j) __stcg(d2 + j, __ldg(s2 + j));
   } else {
     for (uint32_t j = 0; j < t.dim; ++j) __stcg(dst + j, __ldg(src + j));
   }
@@ -584,7 +589,7 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
             s.mi[u] = (uint32_t)i;
           }
         } else if (values && !s.keep_hits) {
-          copy_row<G, VEC16, false>(value_ptr(t, g), values + i * t.dim, t.dim, lane_g);
+          copy_row<G, VEC16, false>(value_ptr(t, g), values + i * t.dim, t.dim, lane_g, t.vec8);
         }
         if (lane_g == 0) {
           update_resident_score(t, g, m, scores_in != nullptr, scores_in ? __ldg(scores_in + i) : 0,
@@ -630,7 +635,8 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
             s.mi[u] = (uint32_t)i;
           }
         } else {
-          copy_row<G, VEC16, false>(value_ptr(t, gc), values + i * t.dim, t.dim, lane_g);
+          copy_row<G, VEC16, false>(value_ptr(t, gc), values + i * t.dim, t.dim, lane_g,
+                                    t.vec8);
         }
       }
     }
@@ -703,6 +709,11 @@ __device__ __forceinline__ void fill_slot(const TableDev& t, uint64_t g, uint64_
     const float4* s4 = reinterpret_cast<const float4*>(src);
     float4* d4 = reinterpret_cast<float4*>(dst);
     for (uint32_t j = lane; j < (t.dim >> 2); j += 32) __stcg(d4 + j, __ldg(s4 + j));
+  } else if (t.vec8 && (t.dim & 1) == 0 &&
+             ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 7) == 0) {
+    const float2* s2 = reinterpret_cast<const float2*>(src);
+    float2* d2 = reinterpret_cast<float2*>(dst);
+    for (uint32_t j = lane; j < (t.dim >> 1); j += 32) __stcg(d2 + j, __ldg(s2 + j));
   } else {
     for (uint32_t j = lane; j < t.dim; j += 32) __stcg(dst + j, __ldg(src + j));
   }
@@ -1231,7 +1242,7 @@ __global__ void __launch_bounds__(kFlushThreads)
     const uint64_t g = s.gdefer[u];
     if (__ldcg(reinterpret_cast<const unsigned long long*>(key_ptr(t, g))) != s.mkey[u]) continue;
     copy_row<kFlushLanes, VEC16, false>(value_ptr(t, g), values + (uint64_t)s.mi[u] * t.dim,
-                                        t.dim, lane_g);
+                                        t.dim, lane_g, t.vec8);
   }
 }
 
@@ -1491,8 +1502,7 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
   a.s.keep_hits = keep_hits ? 1 : 0;
   a.s.row_prefetch = in_device_memory(values) ? 1 : 0;
   const Scratch& s = a.s;
-  const bool vec16 = t->dev.dim % 4 == 0 && aligned16(values) &&
-                     (gather_src == nullptr || aligned16(gather_src));
+  const bool vec16 = row_vector_bytes(t, values, gather_src) == 16;
   launch_dedup(t, n, keys, s, st);
   if (gather_src) {
     // values is the staging array: fill the rows the later phases read
@@ -1549,7 +1559,7 @@ hkv_status launch_assign(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
   ScratchAlloc a;
   hkv_status rc = alloc_scratch(t, n, false, false, st, &a);
   if (rc) return rc;
-  const bool vec16 = t->dev.dim % 4 == 0 && (values == nullptr || aligned16(values));
+  const bool vec16 = row_vector_bytes(t, values) == 16;
   launch_dedup(t, n, keys, a.s, st);
   launch_update<false>(t, n, a.s, values, scores, ctx, vec16, st);
   cudaFreeAsync(a.base, st);
@@ -1641,7 +1651,7 @@ hkv_status launch_upsert_in(hkv_table_s* t, uint64_t n, const uint64_t* keys, co
   cudaMemsetAsync(s.tab, 0xFF, (s.tab_mask + 1) * sizeof(DedupEntry), st);
   cudaMemsetAsync(s.cnt, 0, kCntWords * 8, st);
   s.row_prefetch = in_device_memory(values) ? 1 : 0;
-  const bool vec16 = t->dev.dim % 4 == 0 && aligned16(values);
+  const bool vec16 = row_vector_bytes(t, values) == 16;
   launch_dedup(t, n, keys, s, st);
   launch_update<true>(t, n, s, values, scores, ctx, vec16, st);
   {
@@ -1700,7 +1710,7 @@ hkv_status launch_upsert_desc(hkv_table_s* t, uint64_t n_max, const OpDesc* d, v
     return HKV_ERR_INVALID_ARG;
   }
   s.d = d;
-  const bool vec16 = t->dev.dim % 4 == 0;
+  const bool vec16 = row_vector_bytes(t, nullptr) == 16;  // rows checked 16-byte aligned
   clear_kernel<<<grid_for(t, s.tab_mask + 1, 256, 8), 256, 0, st>>>(s);
   launch_dedup(t, n, nullptr, s, st);
   launch_update<true>(t, n, s, nullptr, nullptr, ScoreCtx{0, 0}, vec16, st);
