@@ -84,7 +84,7 @@ def build_sim(force: bool = False) -> str:
     deps = [src, os.path.join(CSRC, "sched.hpp")]
     if force or _newer(SIM, deps):
         tmp = SIM + f".tmp{os.getpid()}"
-        _run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, src])
+        _run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", "-o", tmp, src])
         os.replace(tmp, SIM)
     return SIM
 

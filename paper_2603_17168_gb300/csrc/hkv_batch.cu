@@ -192,17 +192,15 @@ hkv_status hkv_batch_run(hkv_batch_t b, const hkv_batch_op* ops, int use_graph,
     if (o.op == HKV_OP_UPSERT && o.n) d.step = ++t->step;
     hd[i] = d;
   }
-  // take every table's role on the caller's stream (tables locked in address
+  // take every table's role on the caller's stream (tables taken in address
   // order, so concurrent rounds over overlapping tables cannot deadlock)
   std::vector<int> order;
   for (int i = 0; i < b->n; ++i)
     if (ops[i].op != HKV_OP_NONE) order.push_back(i);
   std::sort(order.begin(), order.end(),
             [&](int x, int y) { return b->tables[x] < b->tables[y]; });
-  std::vector<std::unique_lock<std::mutex>> locks;
   for (int i : order)
-    locks.push_back(b->tables[i]->sched.acquire(
-        ops[i].op == HKV_OP_FIND ? hkv::kReader : hkv::kInserter, s));
+    b->tables[i]->sched.acquire(ops[i].op == HKV_OP_FIND ? hkv::kReader : hkv::kInserter, s);
   cudaMemcpyAsync(b->desc_dev, hd, b->n * sizeof(OpDesc), cudaMemcpyHostToDevice, s);
   cudaEventRecord(b->ring_ev[r], s);
 

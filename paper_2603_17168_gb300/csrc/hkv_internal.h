@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -109,8 +110,10 @@ struct hkv_table_s {
   uint64_t capacity = 0;
   uint64_t slots_per_slice = 0;
   uint64_t hbm_value_slots = 0;
-  uint64_t step = 0;
-  uint64_t epoch = 0;
+  // Table step and epoch: atomic, since calls of a compatible group (assign
+  // from several threads) run their host code concurrently.
+  std::atomic<uint64_t> step{0};
+  std::atomic<uint64_t> epoch{0};
   hkv::LaunchCfg launch;
   void* meta = nullptr;                 // digests + keys + scores + err + counters
   std::vector<void*> hbm_slices;

@@ -74,8 +74,8 @@ extern "C" hkv_status hkv_insert_or_assign_noalloc(hkv_table_t t, uint64_t n,
   hkv_status rc = scratch_address(&scratch);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  auto lk = t->sched.acquire(hkv::kInserter, s);
-  hkv::ScoreCtx ctx{n ? t->step + 1 : t->step, t->epoch};
+  t->sched.acquire(hkv::kInserter, s);
+  hkv::ScoreCtx ctx{n ? t->step.load() + 1 : t->step.load(), t->epoch.load()};
   rc = hkv::launch_upsert_in(t, n, keys, values, (t->opts.policy == HKV_CUSTOM) ? scores : nullptr,
                              status_out, evicted_keys, evicted_scores, n_evicted, ctx, scratch,
                              kNoAllocScratchBytes, s);

@@ -418,7 +418,7 @@ hkv_status hkv_find(hkv_table_t t, uint64_t n, const uint64_t* keys, float* valu
                     uint8_t* found, uint64_t* scores_out, hkv_stream_t stream) {
   if (bad(t) || (n && (!keys || !values_out))) return fail(HKV_ERR_INVALID_ARG, "find arguments");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  auto lk = t->sched.acquire(kReader, s);
+  t->sched.acquire(kReader, s);
   hkv_status rc = launch_find(t, n, keys, values_out, found, scores_out, s);
   t->sched.release(s);
   return rc;
@@ -428,7 +428,7 @@ hkv_status hkv_contains(hkv_table_t t, uint64_t n, const uint64_t* keys, uint8_t
                         hkv_stream_t stream) {
   if (bad(t) || (n && (!keys || !found))) return fail(HKV_ERR_INVALID_ARG, "contains arguments");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  auto lk = t->sched.acquire(kReader, s);
+  t->sched.acquire(kReader, s);
   hkv_status rc = launch_find(t, n, keys, nullptr, found, nullptr, s);
   t->sched.release(s);
   return rc;
@@ -444,8 +444,8 @@ hkv_status hkv_insert_or_assign(hkv_table_t t, uint64_t n, const uint64_t* keys,
     return fail(HKV_ERR_INVALID_ARG, "HKV_CUSTOM needs scores");
   if (n >= (1ull << 31)) return fail(HKV_ERR_INVALID_ARG, "batch above 2^31 keys");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  auto lk = t->sched.acquire(kInserter, s);
-  ScoreCtx ctx{n ? t->step + 1 : t->step, t->epoch};
+  t->sched.acquire(kInserter, s);
+  ScoreCtx ctx{n ? t->step.load() + 1 : t->step.load(), t->epoch.load()};
   hkv_status rc = launch_upsert(t, n, keys, values,
                                 (t->opts.policy == HKV_CUSTOM) ? scores : nullptr, status_out,
                                 evicted_keys, evicted_scores, evicted_values, n_evicted, ctx, s);
@@ -462,8 +462,8 @@ hkv_status hkv_find_or_insert(hkv_table_t t, uint64_t n, const uint64_t* keys, f
     return fail(HKV_ERR_INVALID_ARG, "HKV_CUSTOM needs scores");
   if (n >= (1ull << 31)) return fail(HKV_ERR_INVALID_ARG, "batch above 2^31 keys");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  auto lk = t->sched.acquire(kInserter, s);
-  ScoreCtx ctx{n ? t->step + 1 : t->step, t->epoch};
+  t->sched.acquire(kInserter, s);
+  ScoreCtx ctx{n ? t->step.load() + 1 : t->step.load(), t->epoch.load()};
   hkv_status rc = launch_find_or_insert(t, n, keys, values_io,
                                         (t->opts.policy == HKV_CUSTOM) ? scores : nullptr,
                                         found_out, ctx, s);
@@ -477,11 +477,12 @@ hkv_status hkv_assign(hkv_table_t t, uint64_t n, const uint64_t* keys, const flo
   if (bad(t) || (n && !keys)) return fail(HKV_ERR_INVALID_ARG, "assign arguments");
   if (n >= (1ull << 31)) return fail(HKV_ERR_INVALID_ARG, "batch above 2^31 keys");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  auto lk = t->sched.acquire(kUpdater, s);
-  ScoreCtx ctx{n ? t->step + 1 : t->step, t->epoch};
+  t->sched.acquire(kUpdater, s);
+  // updaters run concurrently: each reserves its step (a failed launch
+  // still advances it)
+  ScoreCtx ctx{n ? t->step.fetch_add(1) + 1 : t->step.load(), t->epoch.load()};
   hkv_status rc = launch_assign(t, n, keys, values,
                                 (t->opts.policy == HKV_CUSTOM) ? scores : nullptr, ctx, s);
-  if (rc == HKV_OK && n) t->step++;
   t->sched.release(s);
   return rc;
 }
@@ -489,7 +490,7 @@ hkv_status hkv_assign(hkv_table_t t, uint64_t n, const uint64_t* keys, const flo
 hkv_status hkv_erase(hkv_table_t t, uint64_t n, const uint64_t* keys, hkv_stream_t stream) {
   if (bad(t) || (n && !keys)) return fail(HKV_ERR_INVALID_ARG, "erase arguments");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  auto lk = t->sched.acquire(kInserter, s);
+  t->sched.acquire(kInserter, s);
   hkv_status rc = launch_erase(t, n, keys, s);
   t->sched.release(s);
   return rc;
@@ -510,8 +511,8 @@ hkv_status hkv_copy_state(hkv_table_t dst, hkv_table_t src, hkv_stream_t stream)
   // opposite directions cannot wait on each other.
   hkv_table_s* first = dst < src ? dst : src;
   hkv_table_s* second = dst < src ? src : dst;
-  auto l1 = first->sched.acquire(first == dst ? kInserter : kReader, s);
-  auto l2 = second->sched.acquire(second == dst ? kInserter : kReader, s);
+  first->sched.acquire(first == dst ? kInserter : kReader, s);
+  second->sched.acquire(second == dst ? kInserter : kReader, s);
   // digests, (key, score) pairs and occupancy counters: the metadata up to
   // the error word, which sits at the same offset in both tables
   const uint64_t meta = reinterpret_cast<const char*>(src->dev.err) -
@@ -523,8 +524,8 @@ hkv_status hkv_copy_state(hkv_table_t dst, hkv_table_t src, hkv_stream_t stream)
                     cudaMemcpyDeviceToDevice, s);
   for (size_t i = 0; i < src->host_slices.size(); ++i)
     cudaMemcpyAsync(dst->host_slices[i], src->host_slices[i], slice_bytes, cudaMemcpyDefault, s);
-  dst->step = src->step;
-  dst->epoch = src->epoch;
+  dst->step = src->step.load();
+  dst->epoch = src->epoch.load();
   const hkv_status rc = cuda_status(cudaGetLastError(), "copy_state");
   second->sched.release(s);
   first->sched.release(s);
@@ -536,7 +537,7 @@ hkv_status hkv_size(hkv_table_t t, uint64_t* out, hkv_stream_t stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned long long* d = t->dev.counters + 28;  // spare words after the counters
   {
-    auto lk = t->sched.acquire(kReader, s);
+    t->sched.acquire(kReader, s);
     hkv_status rc = launch_size(t, d, s);
     t->sched.release(s);
     if (rc) return rc;
@@ -556,7 +557,7 @@ hkv_status hkv_export_batch(hkv_table_t t, uint64_t slot_offset, uint64_t n_slot
   if (slot_offset > t->capacity || n_slots > t->capacity - slot_offset)
     return fail(HKV_ERR_INVALID_ARG, "slot range outside the table");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  auto lk = t->sched.acquire(kReader, s);
+  t->sched.acquire(kReader, s);
   hkv_status rc = launch_export(t, slot_offset, n_slots, count_out, keys, values, scores, slots, s);
   t->sched.release(s);
   return rc;
@@ -570,7 +571,7 @@ hkv_status hkv_export_batch_if(hkv_table_t t, uint64_t slot_offset, uint64_t n_s
   if (slot_offset > t->capacity || n_slots > t->capacity - slot_offset)
     return fail(HKV_ERR_INVALID_ARG, "slot range outside the table");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  auto lk = t->sched.acquire(kReader, s);
+  t->sched.acquire(kReader, s);
   hkv_status rc = launch_export(t, slot_offset, n_slots, count_out, keys, values, scores, slots,
                                 s, score_min, score_max);
   t->sched.release(s);
@@ -581,7 +582,7 @@ hkv_status hkv_find_ptr(hkv_table_t t, uint64_t n, const uint64_t* keys, const f
                         uint8_t* found, hkv_stream_t stream) {
   if (bad(t) || (n && (!keys || !ptrs_out))) return fail(HKV_ERR_INVALID_ARG, "find* arguments");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  auto lk = t->sched.acquire(kReader, s);
+  t->sched.acquire(kReader, s);
   hkv_status rc = launch_find_ptr(t, n, keys, ptrs_out, found, s);
   t->sched.release(s);
   return rc;
@@ -602,7 +603,7 @@ hkv_status hkv_set_step(hkv_table_t t, uint64_t step) {
   return HKV_OK;
 }
 
-uint64_t hkv_get_step(hkv_table_t t) { return t ? t->step : 0; }
+uint64_t hkv_get_step(hkv_table_t t) { return t ? t->step.load() : 0; }
 
 hkv_status hkv_set_epoch(hkv_table_t t, uint64_t epoch) {
   if (bad(t)) return fail(HKV_ERR_INVALID_ARG, "null table");
@@ -691,8 +692,8 @@ hkv_status insert_or_assign_gathered(hkv_table_s* t, uint64_t n, const uint64_t*
   if (n && t->opts.policy == HKV_CUSTOM && !scores)
     return fail(HKV_ERR_INVALID_ARG, "HKV_CUSTOM needs scores");
   if (n >= (1ull << 31)) return fail(HKV_ERR_INVALID_ARG, "batch above 2^31 keys");
-  auto lk = t->sched.acquire(kInserter, s);
-  ScoreCtx ctx{n ? t->step + 1 : t->step, t->epoch};
+  t->sched.acquire(kInserter, s);
+  ScoreCtx ctx{n ? t->step.load() + 1 : t->step.load(), t->epoch.load()};
   hkv_status rc = launch_upsert(t, n, keys, rows_stage,
                                 (t->opts.policy == HKV_CUSTOM) ? scores : nullptr, status_out,
                                 nullptr, nullptr, nullptr, nullptr, ctx, s, false, rows_src);

@@ -17,10 +17,22 @@
 // waiting on the current epoch's events orders a newcomer after all earlier
 // incompatible work, transitively.
 //
+// The table's mutex is held only while an operation takes its waits
+// (acquire) and while it records its completion event (release), not while
+// it launches its kernels in between: compatible operations from several
+// host threads launch concurrently. An operation that opens a new epoch
+// first waits, on the host, until every launch of the current epoch has
+// recorded its event (otherwise it would wait on events not yet recorded),
+// and while it waits, newcomers queue behind it, so a stream of compatible
+// operations cannot starve it. Callers that take several tables' roles take
+// them in one global (address) order and release after launching, so the
+// waits cannot form a cycle.
+//
 // Backend supplies: Stream, Event, Event record(Stream), void wait(Stream,
 // Event), bool same(Stream, Stream), void recycle(Event).
 #pragma once
 
+#include <condition_variable>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -45,25 +57,33 @@ class TripleGroup {
   explicit TripleGroup(Backend be = Backend()) : be_(std::move(be)) {}
   ~TripleGroup() { clear(); }
 
-  // Order stream s after all in-flight work incompatible with group g.
-  // Call with the returned lock held until release().
-  std::unique_lock<std::mutex> acquire(Group g, Stream s) {
+  // Order stream s after all in-flight work incompatible with group g. The
+  // caller then launches its work on s and calls release(s).
+  void acquire(Group g, Stream s) {
     std::unique_lock<std::mutex> lk(mu_);
+    cv_.wait(lk, [&] { return !switching_; });
     if (!(have_epoch_ && compatible(group_, g, rw_lock_))) {
+      switching_ = true;
+      cv_.wait(lk, [&] { return launching_ == 0; });
       for (auto& fe : frontier_) be_.recycle(fe.second);
       frontier_ = std::move(current_);
       current_.clear();
       group_ = g;
       have_epoch_ = true;
+      switching_ = false;
+      cv_.notify_all();
     }
     for (auto& fe : frontier_)
       if (!be_.same(fe.first, s)) be_.wait(s, fe.second);
-    return lk;
+    ++launching_;
   }
 
   // Record the completion point of the operation just launched on s.
   void release(Stream s) {
+    std::lock_guard<std::mutex> lk(mu_);
     Event e = be_.record(s);
+    --launching_;
+    if (launching_ == 0) cv_.notify_all();
     for (auto& ce : current_)
       if (be_.same(ce.first, s)) {
         be_.recycle(ce.second);
@@ -95,6 +115,9 @@ class TripleGroup {
  private:
   Backend be_;
   std::mutex mu_;
+  std::condition_variable cv_;
+  int launching_ = 0;        // acquired operations not yet released
+  bool switching_ = false;   // an operation waits to open a new epoch
   bool have_epoch_ = false;
   bool rw_lock_ = false;
   Group group_ = kReader;

@@ -124,3 +124,52 @@ def test_rw_lock_programs_respect_rw_compatibility(sim_rw, seed):
         for j in range(i + 1, n):
             if s[i] == s[j] or not (g[i] == g[j] == R):
                 assert en[i] <= st[j] + 1e-12, (i, j, g[i], g[j])
+
+
+@pytest.fixture(scope="module")
+def sim_threads():
+    L = ctypes.CDLL(B.build_sim(force=True))
+    f = L.hkv_sched_sim_threads
+    P = np.ctypeslib.ndpointer
+    f.argtypes = [ctypes.c_int, ctypes.c_int, P(np.int32), P(np.float64), ctypes.c_int,
+                  ctypes.c_int, P(np.float64), P(np.float64)]
+    f.restype = ctypes.c_int
+
+    def run(groups, dur, rw_lock=0, launch_us=20):
+        g = np.ascontiguousarray(groups, np.int32)
+        n_threads, per = g.shape
+        st, en = np.zeros(g.size), np.zeros(g.size)
+        assert f(n_threads, per, g.ravel(), np.ascontiguousarray(dur, np.float64).ravel(),
+                 rw_lock, launch_us, st, en) == 0
+        return st.reshape(g.shape), en.reshape(g.shape)
+    return run
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("rw_lock", [0, 1])
+def test_threads_launching_concurrently_keep_table4(sim_threads, seed, rw_lock):
+    """Host threads take roles and launch at the same time (the scheduler's
+    mutex is not held while a call launches): no two incompatible ops
+    overlap on the virtual clock, and the run ends (no deadlock)."""
+    rng = np.random.default_rng(seed)
+    n_threads, per = 6, 120
+    # mostly one group at a time, with runs of each, so epochs of several
+    # concurrent members form and are then broken by other groups
+    runs = rng.integers(0, 3, size=(n_threads, per // 10))
+    groups = np.repeat(runs, 10, axis=1)
+    flip = rng.random(groups.shape) < 0.1
+    groups[flip] = rng.integers(0, 3, size=flip.sum())
+    dur = rng.uniform(0.5, 2.0, size=groups.shape)
+    st, en = sim_threads(groups, dur, rw_lock=rw_lock, launch_us=30)
+    g, s, e = groups.ravel(), st.ravel(), en.ravel()
+    owner = np.repeat(np.arange(n_threads), per)
+    ok_pair = (g[:, None] == g[None, :]) & (g[:, None] != I)
+    if rw_lock:
+        ok_pair &= g[:, None] == R
+    overlap = (s[:, None] < e[None, :]) & (s[None, :] < e[:, None])
+    bad = overlap & ~ok_pair & (owner[:, None] != owner[None, :])
+    assert not bad.any(), np.argwhere(bad)[:5]
+    if not rw_lock:
+        # compatible groups did run side by side somewhere
+        both = overlap & ok_pair & (owner[:, None] != owner[None, :])
+        assert both.any()
