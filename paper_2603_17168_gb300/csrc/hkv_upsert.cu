@@ -582,8 +582,9 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
     if (active) {
       if (hit) {
         const uint64_t g = b * kSlots + (uint64_t)slot;
-        if (UPSERT && s.gdefer && !s.evv && g >= s.host_slot0) {
-          // a host-memory row: written later, in region order
+        if (UPSERT && s.gdefer && !s.evv && !s.keep_hits && g >= s.host_slot0) {
+          // a host-memory row: written later, in region order (find_or_insert
+          // keeps a resident's row, so there is nothing to write)
           if (lane_g == 0) {
             s.gdefer[u] = g;
             s.mi[u] = (uint32_t)i;

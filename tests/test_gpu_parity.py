@@ -550,16 +550,25 @@ def test_export_batch_if_matches_filtered_export():
         assert np.array_equal(gv[order].view(np.uint32), ov[sel].view(np.uint32))
 
 
-@pytest.mark.parametrize("policy,dual,det", [(hkv.LFU, False, False), (hkv.CUSTOM, False, False),
-                                             (hkv.LRU, True, True)])
-def test_find_or_insert_bit_exact(policy, dual, det):
+@pytest.mark.parametrize("policy,dual,det,tiered", [(hkv.LFU, False, False, False),
+                                                    (hkv.CUSTOM, False, False, False),
+                                                    (hkv.LRU, True, True, False),
+                                                    (hkv.LFU, False, False, True),
+                                                    (hkv.LRU, True, True, True)])
+def test_find_or_insert_bit_exact(policy, dual, det, tiered):
     """find_or_insert against the oracle's: returned rows, found flags and
     the full state after every batch (Zipf batches with duplicates, or
     distinct keys in deterministic dual-bucket mode), through the point
-    where the table is full and refuses keys."""
+    where the table is full and refuses keys. Tiered: most value rows in
+    host memory, where insert_or_assign defers its row writes; residents
+    must keep their rows."""
     rng = np.random.default_rng(9900 + policy + 10 * dual)
     nb, dim = 32, 4
-    t = hkv.Table(nb * 128, dim, policy, dual_bucket=dual, deterministic=det)
+    budget = dict(hbm_value_budget_bytes=2 * 4 * 128 * dim * 4,
+                  slice_bytes=4 * 128 * dim * 4) if tiered else {}
+    t = hkv.Table(nb * 128, dim, policy, dual_bucket=dual, deterministic=det, **budget)
+    if tiered:
+        assert t.hbm_value_slots == 2 * 4 * 128
     o = oracle.OracleTable(nb, dim, policy, dual)
     z = w.Zipf(1.05, 12000)
     for n in (3000, 0, 1, 5000, 7000, 4096):
