@@ -55,7 +55,10 @@ enum : int {
   kCntPending = 3,
   kCntInsCursor = 4,  // next 32-key chunk of phase I to hand out
   kCntDeferred = 5,   // keys phase U left to phase I (mflag != 0)
-  kCntWords = 8
+  kBarCount = 6,      // ordered phase I in one launch: grid barrier arrivals
+  kBarGen = 7,        // and generation
+  kCntPending2 = 8,   // pending keys of odd / even waves (kCntPending, this)
+  kCntWords = 10
 };
 
 struct Scratch {
@@ -956,13 +959,13 @@ __device__ __forceinline__ unsigned long long wave_tag(uint64_t wave, uint32_t i
   return (wave << 32) | (unsigned long long)(0xFFFFFFFFu - i);
 }
 
-__global__ void __launch_bounds__(kOrdThreads)
-    ordered_bid_kernel(TableDev t, Scratch s, uint64_t wave) {
-  if (aborted(s)) return;
+// Wave `wave`'s bids of every pending key (Algorithm 3 order: the smallest
+// batch index wins each bucket).
+__device__ __forceinline__ void ordered_bid(const TableDev& t, const Scratch& s, uint64_t wave) {
   const uint64_t nu = s.cnt[kCntUnique];
   for (uint64_t u = blockIdx.x * (uint64_t)kOrdThreads + threadIdx.x; u < nu;
        u += (uint64_t)gridDim.x * kOrdThreads) {
-    if (s.mflag[u] != 1) continue;
+    if (__ldcg(s.mflag + u) != 1) continue;
     const uint64_t key = s.mkey[u];
     const uint64_t b1 = fmix64(key) & t.bucket_mask;
     const uint64_t b2 = t.dual ? second_bucket(t, key) : b1;
@@ -972,6 +975,12 @@ __global__ void __launch_bounds__(kOrdThreads)
   }
 }
 
+__global__ void __launch_bounds__(kOrdThreads)
+    ordered_bid_kernel(TableDev t, Scratch s, uint64_t wave) {
+  if (aborted(s)) return;
+  ordered_bid(t, s, wave);
+}
+
 // A warp of the ordered phase I takes 32 consecutive u. Every lane checks
 // whether its key won both buckets this wave; winners with a free slot take
 // it alone (D1), winners whose candidates are full run the D2 victim search
@@ -979,18 +988,19 @@ __global__ void __launch_bounds__(kOrdThreads)
 // buckets, one warp argmin, admission, replacement. A winner owns its
 // buckets for the wave, so nothing here locks or re-checks.
 template <bool VEC16>
-__global__ void __launch_bounds__(kOrdThreads)
-    ordered_insert_kernel(TableDev t, Scratch s, const float* __restrict__ values,
-                          const uint64_t* __restrict__ scores_in, ScoreCtx ctx, uint64_t wave) {
-  if (aborted(s)) return;
+__device__ __forceinline__ void ordered_insert(const TableDev& t, const Scratch& s,
+                                               const float* __restrict__ values,
+                                               const uint64_t* __restrict__ scores_in,
+                                               const ScoreCtx& ctx, uint64_t wave,
+                                               unsigned& pending, unsigned& inserted,
+                                               unsigned& evicted, unsigned& rejected) {
   const int lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * (uint64_t)kOrdThreads + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * kOrdThreads) >> 5;
   const uint64_t nu = s.cnt[kCntUnique];
-  unsigned pending = 0, inserted = 0, evicted = 0, rejected = 0;
   for (uint64_t c = warp; c * 32 < nu; c += nwarps) {
     const uint64_t u = c * 32 + lane;
-    bool won = u < nu && s.mflag[u] == 1;
+    bool won = u < nu && __ldcg(s.mflag + u) == 1;
     uint64_t key = 0, b1 = 0, b2 = 0, sc = 0;
     uint32_t i = 0, e = 0, dg = 0;
     bool full = false;
@@ -1096,11 +1106,91 @@ __global__ void __launch_bounds__(kOrdThreads)
       if (lane == 0) s.mflag[uu] = 2;
     }
   }
+}
+
+template <bool VEC16>
+__global__ void __launch_bounds__(kOrdThreads)
+    ordered_insert_kernel(TableDev t, Scratch s, const float* __restrict__ values,
+                          const uint64_t* __restrict__ scores_in, ScoreCtx ctx, uint64_t wave) {
+  if (aborted(s)) return;
+  unsigned pending = 0, inserted = 0, evicted = 0, rejected = 0;
+  ordered_insert<VEC16>(t, s, values, scores_in, ctx, wave, pending, inserted, evicted, rejected);
   const int which[3] = {HKV_CNT_INSERTED, HKV_CNT_EVICTED, HKV_CNT_REJECTED};
   const unsigned vals[3] = {inserted, evicted, rejected};
   flush_counts(t, which, vals);
   const unsigned long long p = block_reserve(s.cnt + kCntPending, pending);
   (void)p;
+}
+
+// All waves in one cooperative launch (every block resident): bid pass,
+// grid barrier, insert pass, grid barrier, and stop when the wave left no
+// key pending. Removes two launches per wave and the host's check every few
+// waves. The pending count alternates between two words by wave parity:
+// block 0 clears the next wave's word after this wave's first barrier, when
+// every block has read it. Flags other blocks write are read from L2.
+constexpr unsigned kBarrierSpins = 1u << 22;  // 64-ns naps: ~0.3 s, then give up
+
+// Grid-wide barrier; false (after latching HKV_ERR_TIMEOUT and aborting the
+// batch) if the other blocks did not all arrive within the bound.
+__device__ bool grid_barrier(const Scratch& s, uint32_t* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned long long* gen = s.cnt + kBarGen;
+    const unsigned long long g = *gen;
+    __threadfence();
+    if (atomicAdd(s.cnt + kBarCount, 1ull) == gridDim.x - 1) {
+      atomicExch(s.cnt + kBarCount, 0ull);
+      __threadfence();
+      atomicAdd(s.cnt + kBarGen, 1ull);
+    } else {
+      unsigned it = 0;
+      while (*gen == g) {
+        if (++it > kBarrierSpins) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (!ok) abort_batch(s, err, HKV_ERR_TIMEOUT);
+  }
+  __syncthreads();
+  const int r = ok;
+  __syncthreads();
+  return r != 0;
+}
+
+template <bool VEC16>
+__global__ void __launch_bounds__(kOrdThreads)
+    ordered_waves_kernel(TableDev t, Scratch s, const float* __restrict__ values,
+                         const uint64_t* __restrict__ scores_in, ScoreCtx ctx) {
+  unsigned inserted = 0, evicted = 0, rejected = 0;
+  const uint64_t nu = s.cnt[kCntUnique];
+  // each wave places the smallest pending key, so nu waves always suffice
+  __shared__ int stop;
+  for (uint64_t wave = 1; wave <= nu; ++wave) {
+    // one decision per block: another block may abort between two reads
+    __syncthreads();
+    if (threadIdx.x == 0) stop = aborted(s) ? 1 : 0;
+    __syncthreads();
+    if (stop) break;
+    unsigned long long* pend = s.cnt + ((wave & 1) ? kCntPending : kCntPending2);
+    unsigned long long* next = s.cnt + ((wave & 1) ? kCntPending2 : kCntPending);
+    ordered_bid(t, s, wave);
+    if (!grid_barrier(s, t.err)) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *next = 0;
+    unsigned pw = 0;
+    ordered_insert<VEC16>(t, s, values, scores_in, ctx, wave, pw, inserted, evicted, rejected);
+    block_reserve(pend, pw);
+    if (!grid_barrier(s, t.err)) break;
+    if (__ldcg(pend) == 0) break;
+  }
+  const int which[3] = {HKV_CNT_INSERTED, HKV_CNT_EVICTED, HKV_CNT_REJECTED};
+  const unsigned vals[3] = {inserted, evicted, rejected};
+  flush_counts(t, which, vals);
 }
 
 // ------------------------------------------------- gather of input rows
@@ -1464,6 +1554,29 @@ hkv_status run_ordered_phase_i(hkv_table_s* t, uint64_t n, const Scratch& s, con
                                const uint64_t* scores, ScoreCtx ctx, bool vec16,
                                cudaStream_t st) {
   KernelTimer timer(t->prof, HKV_K_INSERT, st);
+  {
+    // all waves in one cooperative launch, one grid of resident blocks
+    void (*k)(TableDev, Scratch, const float*, const uint64_t*, ScoreCtx) =
+        vec16 ? ordered_waves_kernel<true> : ordered_waves_kernel<false>;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kOrdThreads, 0) ==
+            cudaSuccess &&
+        per_sm > 0) {
+      TableDev dv = t->dev;
+      Scratch sv = s;
+      const float* vv = values;
+      const uint64_t* sc = scores;
+      ScoreCtx cv = ctx;
+      void* args[] = {&dv, &sv, &vv, &sc, &cv};
+      const unsigned grid = (unsigned)std::max<uint64_t>(
+          1, std::min<uint64_t>((uint64_t)t->num_sms * (unsigned)per_sm,
+                                (n + kOrdThreads - 1) / kOrdThreads));
+      if (cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k), grid, kOrdThreads, args, 0, st) ==
+          cudaSuccess)
+        return HKV_OK;
+    }
+    cudaGetLastError();  // refused: fall back to one launch pair per wave
+  }
   const unsigned og = grid_for(t, n, kOrdThreads, 8);
   for (uint64_t wave = 1;; ) {
     for (int k = 0; k < kWavesPerCheck; ++k, ++wave) {
