@@ -1090,6 +1090,7 @@ def run_tiered(args):
     t0 = time.time()
     t = hkv.Table(slots, dim, hkv.CUSTOM_TS_FREQ, hbm_value_budget_bytes=budget)
     create_s = time.time() - t0
+    host_mem = t.host_memory_info()
     batch = args.batch
     t.set_epoch(1)
     t1 = time.time()
@@ -1177,6 +1178,9 @@ def run_tiered(args):
                       "host_value_gib": round((t.capacity - t.hbm_value_slots) * dim * 4 / (1 << 30), 2),
                       "value_slots_in_hbm_frac": round(hbm_frac, 4), "batch": batch,
                       "create_s": round(create_s, 1), "fill_s": round(fill_s, 1),
+                      "host_huge_page_frac": round(host_mem["huge_bytes"] /
+                                                   max(1, host_mem["host_bytes"]), 4),
+                      "host_one_mapping": host_mem["one_mapping"],
                       "lambda_fill": round(lam, 4)},
            "find_bkvs": round(args.steps * batch / f_ms / 1e6, 4),
            "upsert_bkvs": round(args.steps * batch / u_ms / 1e6, 4),

@@ -116,7 +116,14 @@ hkv_status hkv_destroy(hkv_table_t t);
 uint64_t hkv_capacity(hkv_table_t t);    /* B * 128 */
 uint64_t hkv_num_buckets(hkv_table_t t); /* B */
 uint32_t hkv_dim(hkv_table_t t);
-uint64_t hkv_hbm_value_slots(hkv_table_t t); /* slots whose values sit in HBM */
+uint64_t hkv_hbm_value_slots(hkv_table_t t);
+/* Host side of a tiered table (a diagnostic): value bytes in host memory,
+ * how many of them transparent huge pages backed when the table was created
+ * (scattered host rows are bound by the device's address translation, so
+ * the page size matters), and whether the host slices are one registered
+ * mapping (1) or cudaHostAlloc slices (0). */
+hkv_status hkv_host_memory_info(hkv_table_t t, uint64_t *host_bytes, uint64_t *huge_bytes,
+                                int *one_mapping); /* slots whose values sit in HBM */
 
 /* find (reader; Algorithm 1): for each keys[i], probe its bucket(s) through
  * the digest line and copy the value of a hit to values_out[i]
@@ -508,7 +515,9 @@ enum {
   HKV_K_ERASE = 6,
   HKV_K_EXPORT = 7,
   HKV_K_SIZE = 8,
-  HKV_KERNEL_KINDS = 9
+  HKV_K_HOSTROWS = 9,  /* tiered tables: host-memory rows grouped by region
+                          and moved (find's host hits, upsert's deferred rows) */
+  HKV_KERNEL_KINDS = 10
 };
 hkv_status hkv_profile_enable(hkv_table_t t, int on);
 hkv_status hkv_profile_read(hkv_table_t t, double *ms_out, uint64_t *launches_out);

@@ -23,7 +23,7 @@ COUNTER_NAMES = ("find_hit", "find_miss", "unique", "updated", "inserted", "evic
                  "ins_lines", "ins_score_lines", "ins_keys", "timeout_free", "timeout_evict",
                  "timeout_why", "timeout_key", "upd_claims", "upd_claim_lines")
 KERNEL_NAMES = ("find", "dedup", "update", "insert", "reconcile", "status", "erase", "export",
-                "size")
+                "size", "hostrows")
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "RESERVED_KEY", 3: "DUPLICATE_KEY", 4: "OOM",
                 5: "CUDA", 6: "TIMEOUT", 7: "BUSY"}
 SLOTS = 128
@@ -87,6 +87,7 @@ SIGNATURES = {
     "hkv_reset_counters": (_i32, [_vp, _vp]),
     "hkv_set_launch": (_i32, [_vp, _i32, _i32]),
     "hkv_set_value_vector": (_i32, [_vp, _i32]),
+    "hkv_host_memory_info": (_i32, [_vp, _P64, _P64, ctypes.POINTER(ctypes.c_int)]),
     "hkv_find_ptr": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp]),
     "hkv_find_or_insert": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp, _vp]),
     "hkv_gather_rows": (_i32, [_vp, _u64, _u32, _vp, _vp]),
@@ -395,6 +396,15 @@ class Table:
     def set_launch(self, find_threads_per_key: int = 0, update_threads_per_key: int = 0):
         _check(load_library().hkv_set_launch(self._h, find_threads_per_key,
                                              update_threads_per_key))
+
+    def host_memory_info(self) -> dict:
+        """Host side of a tiered table: value bytes in host memory, the bytes
+        of them huge pages backed at creation, one registered mapping or not
+        (hkv_host_memory_info)."""
+        hb, hu, one = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int()
+        _check(load_library().hkv_host_memory_info(self._h, ctypes.byref(hb), ctypes.byref(hu),
+                                                   ctypes.byref(one)))
+        return {"host_bytes": hb.value, "huge_bytes": hu.value, "one_mapping": bool(one.value)}
 
     def set_value_vector(self, nbytes: int = 0):
         """Widest vector (16, 8 or 4 bytes; 0: default 16) of the value-row

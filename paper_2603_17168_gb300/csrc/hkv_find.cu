@@ -124,7 +124,6 @@ void launch_g(const hkv_table_s* t, uint64_t n, const uint64_t* keys, float* out
 hkv_status launch_find(hkv_table_s* t, uint64_t n, const uint64_t* keys, float* values_out,
                        uint8_t* found, uint64_t* scores_out, cudaStream_t s) {
   if (n == 0) return HKV_OK;
-  KernelTimer timer(t->prof, HKV_K_FIND, s);
   const bool vec16 = row_vector_bytes(t, values_out) == 16;
   // host rows of a tiered table: listed by the probe, copied in region order
   void* scratch = nullptr;
@@ -139,6 +138,8 @@ hkv_status launch_find(hkv_table_s* t, uint64_t n, const uint64_t* keys, float* 
     }
     hslot = static_cast<uint64_t*>(scratch);
   }
+  {
+  KernelTimer timer(t->prof, HKV_K_FIND, s);
   switch (t->launch.find_tpk) {
     case 1: launch_g<1>(t, n, keys, values_out, found, scores_out, vec16, s, nullptr, false, nullptr, hslot); break;
     case 2: launch_g<2>(t, n, keys, values_out, found, scores_out, vec16, s, nullptr, false, nullptr, hslot); break;
@@ -147,7 +148,9 @@ hkv_status launch_find(hkv_table_s* t, uint64_t n, const uint64_t* keys, float* 
     case 32: launch_g<32>(t, n, keys, values_out, found, scores_out, vec16, s, nullptr, false, nullptr, hslot); break;
     default: launch_g<8>(t, n, keys, values_out, found, scores_out, vec16, s, nullptr, false, nullptr, hslot); break;
   }
+  }
   if (hslot) {
+    KernelTimer timer(t->prof, HKV_K_HOSTROWS, s);
     RegionOrder ro;
     const uint64_t hb = (n * 8 + 255) & ~255ull;
     hkv_status rc = region_sort(t, hslot, n, nullptr, static_cast<char*>(scratch) + hb, &ro, s);

@@ -123,6 +123,7 @@ struct hkv_table_s {
   void* host_map = nullptr;
   uint64_t host_map_bytes = 0;
   void* host_base = nullptr;            // first host slice inside host_map
+  uint64_t host_huge_bytes = 0;         // of it backed by huge pages at creation
   float** slices_dev = nullptr;
   cudaMemPool_t pool = nullptr;         // stream-ordered scratch allocations
   hkv::TripleGroup<hkv::CudaEvents> sched;

@@ -26,6 +26,29 @@ namespace hkv {
 namespace {
 thread_local std::string g_last_error;
 
+// Bytes of [p, p + len) backed by transparent huge pages, summed over the
+// process's mappings that overlap it (/proc/self/smaps; 0 if unreadable).
+uint64_t huge_page_bytes(const void* p, uint64_t len) {
+  FILE* f = fopen("/proc/self/smaps", "r");
+  if (!f) return 0;
+  const uintptr_t lo = reinterpret_cast<uintptr_t>(p), hi = lo + len;
+  char line[512];
+  bool in = false;
+  uint64_t total = 0;
+  while (fgets(line, sizeof line, f)) {
+    unsigned long a = 0, b = 0;
+    char c = 0;
+    if (sscanf(line, "%lx-%lx%c", &a, &b, &c) == 3 && c == ' ') {
+      in = a < hi && lo < b;
+    } else if (in && strncmp(line, "AnonHugePages:", 14) == 0) {
+      unsigned long kb = 0;
+      if (sscanf(line + 14, "%lu", &kb) == 1) total += (uint64_t)kb << 10;
+    }
+  }
+  fclose(f);
+  return total;
+}
+
 constexpr uint64_t kDefaultSlice = 1ull << 30;
 
 __global__ void init_meta_kernel(uint8_t* digests, uint64_t* kv, uint64_t slots) {
@@ -294,6 +317,7 @@ hkv_status hkv_create(const hkv_options* o, hkv_table_t* out) {
         t->host_map = m;
         t->host_map_bytes = host_bytes + align;
         t->host_base = base;
+        t->host_huge_bytes = huge_page_bytes(base, host_bytes);
         host_dev = static_cast<char*>(dp);
       } else {
         if (reg) cudaHostUnregister(base);
@@ -413,6 +437,16 @@ uint64_t hkv_capacity(hkv_table_t t) { return t ? t->capacity : 0; }
 uint64_t hkv_num_buckets(hkv_table_t t) { return t ? t->num_buckets : 0; }
 uint32_t hkv_dim(hkv_table_t t) { return t ? t->opts.dim : 0; }
 uint64_t hkv_hbm_value_slots(hkv_table_t t) { return t ? t->hbm_value_slots : 0; }
+
+hkv_status hkv_host_memory_info(hkv_table_t t, uint64_t* host_bytes, uint64_t* huge_bytes,
+                                int* one_mapping) {
+  if (bad(t) || !host_bytes || !huge_bytes || !one_mapping)
+    return fail(HKV_ERR_INVALID_ARG, "host memory info arguments");
+  *host_bytes = (t->capacity - t->hbm_value_slots) * (uint64_t)t->opts.dim * 4;
+  *huge_bytes = t->host_huge_bytes;
+  *one_mapping = t->host_map ? 1 : 0;
+  return HKV_OK;
+}
 
 hkv_status hkv_find(hkv_table_t t, uint64_t n, const uint64_t* keys, float* values_out,
                     uint8_t* found, uint64_t* scores_out, hkv_stream_t stream) {

@@ -1640,7 +1640,10 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
     else
       launch_table_kernel(t, insert_kernel<false>, ig, kInsThreads, 0, st, t->dev, s, values,
                           scores, ctx);
-    if (s.gdefer) {
+  }
+  if (s.gdefer) {
+    {
+      KernelTimer timer(t->prof, HKV_K_HOSTROWS, st);
       RegionOrder ro;
       rc = region_sort(t, s.gdefer, n, s.cnt + kCntUnique, a.region, &ro, st);
       if (rc) {
