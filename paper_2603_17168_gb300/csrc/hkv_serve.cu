@@ -361,7 +361,10 @@ hkv_status hkv_serve_run(hkv_server_t s, const hkv_serve_request* reqs, uint64_t
           S.batched_rounds++;
         }
         timing_ev(rd, st);
-        if (rc) break;
+        if (rc) {
+          retire_timing(rd);  // back to the pool (the run ends with rc)
+          break;
+        }
         cudaEvent_t computed = get_ev();
         cudaEventRecord(computed, st);
         cudaStreamWaitEvent(out, computed, 0);
@@ -390,7 +393,10 @@ hkv_status hkv_serve_run(hkv_server_t s, const hkv_serve_request* reqs, uint64_t
         timing_ev(rd, st);
         timing_ev(rd, st);  // copies back follow on the same stream
         S.direct_rounds++;
-        if (rc) break;
+        if (rc) {
+          retire_timing(rd);
+          break;
+        }
       }
       // results back to each request's host buffers, each request with its
       // own completion event in batched mode
