@@ -80,3 +80,91 @@ def test_threads_with_streams_match_serial(rw):
             row = out[i].view(np.uint32)
             assert (np.array_equal(row, old_of[k].view(np.uint32))
                     or np.array_equal(row, new_of[k].view(np.uint32)))
+
+
+def test_inserters_updaters_and_readers_on_their_own_streams():
+    """Host threads, each with its own stream, take their roles and launch at
+    the same time: two insert fresh keys (inserters, exclusive), two assign
+    disjoint resident keys (updaters), two find. LFU scores add up and the
+    key sets are disjoint, so the final state is order-free and must equal
+    the serial application of the same calls. A find of a fresh key returns
+    either a miss or exactly its inserted row (an inserter never overlaps a
+    reader), and a find of an assigned key its old or its new row."""
+    rng = np.random.default_rng(9650)
+    dim = 8
+    nb = 256
+    t = hkv.Table(nb * 128, dim, hkv.LFU)
+    ref = hkv.Table(nb * 128, dim, hkv.LFU)
+    base = w.uniform_keys(rng, 8000, distinct=True)
+    v0 = w.normal_values(rng, base.size, dim)
+    for x in (t, ref):
+        x.insert_or_assign(dev(base), dev(v0))
+    torch.cuda.synchronize()
+    fresh = [w.uniform_keys(rng, 4 * 1024, distinct=True) for _ in range(2)]
+    fresh_vals = [w.normal_values(rng, f.size, dim) for f in fresh]
+    upd = np.array_split(base[:4000], 2)
+    upd_vals = [w.normal_values(rng, u.size, dim) for u in upd]
+    row_of = {}
+    for f, fv in zip(fresh, fresh_vals):
+        row_of.update({int(k): fv[i].tobytes() for i, k in enumerate(f)})
+    old_of = {int(k): v0[i].tobytes() for i, k in enumerate(base)}
+    new_of = {}
+    for u, uv in zip(upd, upd_vals):
+        new_of.update({int(k): uv[i].tobytes() for i, k in enumerate(u)})
+    errors, seen = [], []
+
+    def inserter(f, fv):
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            for c in range(4):
+                sl = slice(c * 1024, (c + 1) * 1024)
+                t.insert_or_assign(dev(f[sl]), dev(fv[sl]))
+        s.synchronize()
+
+    def updater(u, uv):
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            for c in range(0, u.size, 500):
+                t.assign(dev(u[c:c + 500]), dev(uv[c:c + 500]))
+        s.synchronize()
+
+    def reader(q):
+        s = torch.cuda.Stream()
+        for _ in range(6):
+            with torch.cuda.stream(s):
+                out, found, _ = t.find(dev(q))
+            s.synchronize()
+            seen.append((q, host(out).copy(), host(found).astype(bool)))
+
+    q = np.concatenate([fresh[0][:600], fresh[1][:600], base[:1200]])
+    threads = [threading.Thread(target=inserter, args=(f, fv)) for f, fv in zip(fresh, fresh_vals)]
+    threads += [threading.Thread(target=updater, args=(u, uv)) for u, uv in zip(upd, upd_vals)]
+    threads += [threading.Thread(target=reader, args=(q,)) for _ in range(2)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    torch.cuda.synchronize()
+    for qq, out, found in seen:
+        for k, row, f in zip(qq.tolist(), out, found):
+            if k in row_of:
+                if f and row.tobytes() != row_of[k]:
+                    errors.append(("fresh", k))
+            else:
+                if not f or row.tobytes() not in (old_of[k], new_of.get(k, old_of[k])):
+                    errors.append(("resident", k))
+    assert not errors, errors[:5]
+    # the same calls, one after another, on the reference table
+    for f, fv in zip(fresh, fresh_vals):
+        for c in range(4):
+            sl = slice(c * 1024, (c + 1) * 1024)
+            ref.insert_or_assign(dev(f[sl]), dev(fv[sl]))
+    for u, uv in zip(upd, upd_vals):
+        for c in range(0, u.size, 500):
+            ref.assign(dev(u[c:c + 500]), dev(uv[c:c + 500]))
+    torch.cuda.synchronize()
+    gk, gs, gv, gb = export_state(t)
+    rk, rs, rv, rb = export_state(ref)
+    assert np.array_equal(gk, rk) and np.array_equal(gs, rs)
+    assert np.array_equal(gv.view(np.uint32), rv.view(np.uint32))
+    assert t.size() == base.size + sum(f.size for f in fresh)
