@@ -581,20 +581,13 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
       }
     }
     const bool hit = active && slot >= 0;
+    // the slot whose value row this key's group writes below: a hit's own
+    // slot (find_or_insert keeps a resident's row), or the slot a miss claims
     uint64_t gclaim = kNoSlot;
     if (active) {
       if (hit) {
         const uint64_t g = b * kSlots + (uint64_t)slot;
-        if (UPSERT && s.gdefer && !s.evv && !s.keep_hits && g >= s.host_slot0) {
-          // a host-memory row: written later, in region order (find_or_insert
-          // keeps a resident's row, so there is nothing to write)
-          if (lane_g == 0) {
-            s.gdefer[u] = g;
-            s.mi[u] = (uint32_t)i;
-          }
-        } else if (values && !s.keep_hits) {
-          copy_row<G, VEC16, false>(value_ptr(t, g), values + i * t.dim, t.dim, lane_g, t.vec8);
-        }
+        if (values && !s.keep_hits && lane_g == 0) gclaim = g;
         if (lane_g == 0) {
           update_resident_score(t, g, m, scores_in != nullptr, scores_in ? __ldg(scores_in + i) : 0,
                                 ctx);
@@ -628,12 +621,13 @@ __global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm)
         }
       }
     }
-    if (UPSERT) {
-      // the row of a slot claimed above, copied by the key's G lanes (a
-      // host-memory row later, in region order)
+    {
+      // one row copy per warp iteration for hits and claims together, by the
+      // key's G lanes, after the claims (a host-memory row later, in region
+      // order)
       const uint64_t gc = __shfl_sync(kFull, gclaim, group_base);
       if (gc != kNoSlot) {
-        if (s.gdefer && !s.evv && gc >= s.host_slot0) {
+        if (UPSERT && s.gdefer && !s.evv && gc >= s.host_slot0) {
           if (lane_g == 0) {
             s.gdefer[u] = gc;
             s.mi[u] = (uint32_t)i;
