@@ -74,7 +74,7 @@ def parse_args(argv=None):
     p.add_argument("--find-tpk", type=int, default=0)
     p.add_argument("--update-tpk", type=int, default=0)
     p.add_argument("--workload", choices=("single", "multi", "serve", "tiered", "ordered",
-                                          "quality", "concurrency"), default="single")
+                                          "quality", "concurrency", "apis"), default="single")
     p.add_argument("--quality-log2", type=int, default=27,
                    help="log2 slots of the cache-quality tables")
     p.add_argument("--tiered-shrink", type=int, default=0,
@@ -1397,6 +1397,98 @@ def served_record(args):
                       for k, v in r["served"].items()}}
 
 
+def run_apis(args):
+    """Every API by value width and load factor, and find by capacity (the
+    paper's per-API load-factor sweep over its Configs A-C, Sec. 5.2, and its
+    capacity scaling, Sec. 5.3). Tables of 2^27 slots (the paper's 128 M),
+    LRU, dual-bucket, dims 8 / 32 / 64, filled with uniform keys over 2^32;
+    each call takes 2^20 keys, half resident (sampled from the table) and
+    half fresh uniform keys, as in the paper's uniform-key sweep. Per load
+    factor the readers run first (find, find*, contains), then assign of
+    resident keys (updates in place), then insert_or_assign of fresh and
+    resident keys (the only call that moves lambda; its drift is reported).
+    Capacity sweep: find at lambda 0.5, dim 32, 2^24 .. 2^29 slots. Times
+    are the median of `reps` calls, CUDA events on the launching stream."""
+    import torch
+    import paper_2603_17168_gb300 as hkv
+    from paper_2603_17168_gb300 import workloads as w
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(w.seed_for(6))
+    batch, reps = args.batch, max(3, args.steps)
+
+    def med_ms(fn, inputs):
+        fn(inputs[0])
+        torch.cuda.synchronize()
+        ts = []
+        for x in inputs:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn(x)
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    def mixed_batches(t, n_batches):
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        res = torch.empty(t.capacity, dtype=torch.int64, device=dev)
+        t.export_batch(0, t.capacity, res, None, None, None, cnt)
+        n_res = int(cnt.item())
+        out = []
+        for _ in range(n_batches):
+            half = batch // 2
+            pick = torch.randint(0, max(1, n_res), (half,), device=dev, generator=gen)
+            k = torch.cat([res[pick], w.uniform_keys_torch(gen, batch - half, UNIVERSE)])
+            out.append(k[torch.randperm(batch, device=dev, generator=gen)].contiguous())
+        del res
+        return out, n_res
+
+    rate = lambda ms: round(batch / ms / 1e6, 4)  # noqa: E731
+    per_dim = {}
+    for dim in (8, 32, 64):
+        t = hkv.Table(1 << 27, dim, hkv.LRU, dual_bucket=True)
+        rows = {}
+        for lam in (0.5, 1.0):
+            lam_fill = fill_table(t, lam, gen, dim)
+            ks, _ = mixed_batches(t, reps)
+            vals = torch.randn((batch, dim), device=dev, generator=gen)
+            out = torch.empty((batch, dim), device=dev)
+            fl = torch.empty(batch, dtype=torch.uint8, device=dev)
+            ptrs = torch.empty(batch, dtype=torch.int64, device=dev)
+            r = {"lambda_fill": round(lam_fill, 4),
+                 "find": rate(med_ms(lambda k: t.find(k, out, fl), ks)),
+                 "find_ptr": rate(med_ms(lambda k: t.find_ptr(k, ptrs, fl), ks)),
+                 "contains": rate(med_ms(lambda k: t.contains(k, fl), ks)),
+                 "assign": rate(med_ms(lambda k: t.assign(k, vals), ks)),
+                 "insert_or_assign": rate(med_ms(lambda k: t.insert_or_assign(k, vals), ks))}
+            r["lambda_end"] = round(t.size() / t.capacity, 4)
+            rows[str(lam)] = r
+        per_dim[str(dim)] = rows
+        t.close()
+    capacity = {}
+    for log2 in (24, 26, 28, 29):
+        t = hkv.Table(1 << log2, 32, hkv.LRU, dual_bucket=True)
+        fill_table(t, 0.5, gen, 32)
+        ks, _ = mixed_batches(t, reps)
+        out = torch.empty((batch, 32), device=dev)
+        fl = torch.empty(batch, dtype=torch.uint8, device=dev)
+        capacity[f"2^{log2}"] = rate(med_ms(lambda k: t.find(k, out, fl), ks))
+        t.close()
+    cv = list(capacity.values())
+    return {"metric": "B-KV/s per API by value width and load factor; find by capacity",
+            "value": per_dim["32"]["0.5"]["find"], "unit": UNIT, "n_gpus": 1, "steps": reps,
+            "warmup": 1, "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "2^27 slots, LRU, dual-bucket, dims 8/32/64, uniform fill "
+                                   "over 2^32, 2^20-key calls half resident / half fresh; "
+                                   "capacity sweep 2^24..2^29 slots at dim 32, lambda 0.5",
+                       "batch": batch},
+            "per_dim": per_dim, "capacity_find": capacity,
+            "capacity_find_spread": round((max(cv) - min(cv)) / statistics.mean(cv), 4)}
+
+
 def distinct_keys_torch(gen, n, universe, dev):
     """n distinct keys of uniform ranks in [1, universe], in random order."""
     import torch
@@ -1685,6 +1777,10 @@ def main(argv=None):
         import __graft_entry__ as g
         g.build()
         res = run_quality(args)
+    elif args.workload == "apis":
+        import __graft_entry__ as g
+        g.build()
+        res = run_apis(args)
     elif args.workload == "concurrency":
         import __graft_entry__ as g
         g.build()
