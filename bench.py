@@ -1407,6 +1407,9 @@ def run_apis(args):
     factor the readers run first (find, find*, contains), then assign of
     resident keys (updates in place), then insert_or_assign of fresh and
     resident keys (the only call that moves lambda; its drift is reported).
+    find_no_digest / contains_no_digest are the digest ablation (Sec. 5.4,
+    Exp 3a): the same calls comparing every key of a probed bucket instead
+    of reading its digest line first.
     Capacity sweep: find at lambda 0.5, dim 32, 2^24 .. 2^29 slots. Times
     are the median of `reps` calls, CUDA events on the launching stream."""
     import torch
@@ -1462,6 +1465,10 @@ def run_apis(args):
                  "find": rate(med_ms(lambda k: t.find(k, out, fl), ks)),
                  "find_ptr": rate(med_ms(lambda k: t.find_ptr(k, ptrs, fl), ks)),
                  "contains": rate(med_ms(lambda k: t.contains(k, fl), ks)),
+                 # the digest ablation (Exp 3a): every key of a probed bucket compared
+                 "find_no_digest": rate(med_ms(lambda k: t.find_full_keys(k, out, fl), ks)),
+                 "contains_no_digest": rate(med_ms(lambda k: t.find_full_keys(k, None, fl),
+                                                   ks)),
                  "assign": rate(med_ms(lambda k: t.assign(k, vals), ks)),
                  "insert_or_assign": rate(med_ms(lambda k: t.insert_or_assign(k, vals), ks))}
             r["lambda_end"] = round(t.size() / t.capacity, 4)

@@ -154,6 +154,16 @@ hkv_status hkv_gather_rows(const float *const *ptrs, uint64_t n, uint32_t dim, f
 hkv_status hkv_contains(hkv_table_t t, uint64_t n, const uint64_t *keys, uint8_t *found,
                         hkv_stream_t stream);
 
+/* Digest ablation (Sec. 5.4, Exp 3a; a measurement hook): hkv_find (or, with
+ * values_out NULL, hkv_contains) without the digest line. A warp reads each
+ * probed bucket's 2 KiB run of (key, score) pairs and compares every key;
+ * results (rows, found flags) are identical to hkv_find's, the bytes moved
+ * per probed bucket are 2 KiB instead of 128 B plus one key sector per
+ * digest match. Same arguments, roles and errors as hkv_find; tables with
+ * host-memory slices are read in place (no region ordering). */
+hkv_status hkv_find_full_keys(hkv_table_t t, uint64_t n, const uint64_t *keys,
+                              float *values_out, uint8_t *found, hkv_stream_t stream);
+
 /* insert_or_assign (inserter; Algorithms 2 and 3): upsert a batch.
  * Duplicate keys collapse to one entry: the value of the last occurrence,
  * and multiplicity m for the LFU-type policies. Keys resident at batch start

@@ -87,6 +87,7 @@ SIGNATURES = {
     "hkv_reset_counters": (_i32, [_vp, _vp]),
     "hkv_set_launch": (_i32, [_vp, _i32, _i32]),
     "hkv_set_value_vector": (_i32, [_vp, _i32]),
+    "hkv_find_full_keys": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp]),
     "hkv_host_memory_info": (_i32, [_vp, _P64, _P64, ctypes.POINTER(ctypes.c_int)]),
     "hkv_find_ptr": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp]),
     "hkv_find_or_insert": (_i32, [_vp, _u64, _vp, _vp, _vp, _vp, _vp]),
@@ -224,6 +225,20 @@ class Table:
         _check(load_library().hkv_find(self._h, n, _ptr(keys), _ptr(values_out), _ptr(found),
                                        _ptr(scores_out), _stream(stream)))
         return values_out, found, scores_out
+
+    def find_full_keys(self, keys, values_out=None, found=None, stream=None):
+        """find without the digest line (the digest ablation,
+        hkv_find_full_keys): same results as find()."""
+        import torch
+        n = keys.numel()
+        if found is None:
+            found = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        _need(keys, _u64_types(), (n,), "keys")
+        _need(values_out, torch.float32, (n, self.dim), "values_out")
+        _need(found, torch.uint8, (n,), "found")
+        _check(load_library().hkv_find_full_keys(self._h, n, _ptr(keys), _ptr(values_out),
+                                                 _ptr(found), _stream(stream)))
+        return values_out, found
 
     def contains(self, keys, found=None, stream=None):
         import torch

@@ -622,3 +622,41 @@ def test_rows_from_page_locked_host_memory():
     b.sync()
     assert evicted > 0, "no victim search ran"
     same_state(export_state(a), export_state(b))
+
+
+@pytest.mark.parametrize("dual,dim,tiered", [(False, 16, False), (True, 3, False),
+                                             (True, 8, True)])
+def test_find_without_digests_matches_the_oracle(dual, dim, tiered):
+    """The digest ablation (hkv_find_full_keys: every key of a probed bucket
+    compared, no digest line) returns exactly what find returns and what the
+    oracle returns: rows, misses left untouched, found flags; with values
+    NULL it is contains."""
+    rng = np.random.default_rng(9950 + dim + 10 * dual)
+    nb = 64
+    budget = dict(hbm_value_budget_bytes=2 * 4 * 128 * dim * 4,
+                  slice_bytes=4 * 128 * dim * 4) if tiered else {}
+    t = hkv.Table(nb * 128, dim, hkv.LFU, dual_bucket=dual, **budget)
+    o = oracle.OracleTable(nb, dim, oracle.LFU, dual)
+    z = w.Zipf(1.05, 20000)
+    for n in (6000, 9000, 4000):
+        keys = z.keys(rng, n)
+        vals = w.normal_values(rng, n, dim)
+        gpu_upsert(t, keys, vals)
+        o.insert_or_assign(keys, vals)
+    gk, gs, gv, gb = export_state(t)
+    ref = oracle.OracleTable(nb, dim, oracle.LFU, dual)
+    ref.load(gk, gs, gv, gb)
+    q = np.concatenate([z.keys(rng, 5000), w.uniform_keys(rng, 2000)])
+    n = q.size
+    out = nan_filled(n, dim)
+    found = torch.empty(n, dtype=torch.uint8, device="cuda")
+    t.find_full_keys(dev(q), out, found)
+    torch.cuda.synchronize()
+    ov = np.zeros((n, dim), np.uint32)
+    ov[:] = NAN_BITS
+    ov, of, _ = ref.find(q, ov.view(np.float32))
+    assert np.array_equal(host(found).astype(bool), of)
+    assert np.array_equal(host(out).view(np.uint32), ov.view(np.uint32))
+    _, only = t.find_full_keys(dev(q))
+    assert np.array_equal(host(only).astype(bool), of)
+    assert of.sum() > 0
