@@ -128,7 +128,8 @@ hkv_status launch_find(hkv_table_s* t, uint64_t n, const uint64_t* keys, float* 
   // host rows of a tiered table: listed by the probe, copied in region order
   void* scratch = nullptr;
   uint64_t* hslot = nullptr;
-  if (values_out && vec16 && !t->host_slices.empty()) {
+  // (the region order holds 32-bit batch indices: larger finds copy in place)
+  if (values_out && vec16 && !t->host_slices.empty() && n < (1ull << 32)) {
     const uint64_t hb = (n * 8 + 255) & ~255ull;
     if (cudaMallocFromPoolAsync(&scratch, hb + region_sort_bytes(t, n), t->pool, s) !=
         cudaSuccess) {

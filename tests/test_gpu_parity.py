@@ -660,3 +660,35 @@ def test_find_without_digests_matches_the_oracle(dual, dim, tiered):
     _, only = t.find_full_keys(dev(q))
     assert np.array_equal(host(only).astype(bool), of)
     assert of.sum() > 0
+
+
+def test_admission_burst_table9_bit_exact():
+    """Table 9 (Exp 3d) on the GPU, scaled to a full 2^17-slot table: every
+    bucket holds 128 keys with caller scores in [2, 1000); a burst of fresh
+    keys with score 1 is refused whole and leaves the table as it was; the
+    same burst with score 10^9 is admitted whole, each key displacing one of
+    the originals. Statuses, evicted sets and states bit-exact against the
+    oracle."""
+    rng = np.random.default_rng(9970)
+    nb, dim = 1 << 10, 2
+    t = hkv.Table(nb * 128, dim, hkv.CUSTOM)
+    o = oracle.OracleTable(nb, dim, oracle.CUSTOM)
+    keys = w.uniform_keys(rng, nb * 128 * 3, distinct=True)
+    b1, _, _ = oracle.map_keys(nb, False, keys)
+    sel = np.concatenate([np.flatnonzero(b1 == b)[:128] for b in range(nb)])
+    assert sel.size == nb * 128
+    vals = w.normal_values(rng, sel.size, dim)
+    sc = rng.integers(2, 1000, sel.size, dtype=np.uint64)
+    compare_upsert(t, o, keys[sel], vals, sc)
+    assert t.size() == nb * 128
+    before = export_state(t)
+    burst = w.uniform_keys(rng, 32768, distinct=True)
+    bv = w.normal_values(rng, burst.size, dim)
+    st = compare_upsert(t, o, burst, bv, np.full(burst.size, 1, np.uint64))
+    assert np.all(st == hkv.ST_REJECTED)
+    after = export_state(t)
+    assert all(np.array_equal(x, y) for x, y in zip(before, after))
+    st = compare_upsert(t, o, burst, bv, np.full(burst.size, 10**9, np.uint64))
+    assert np.all(st == hkv.ST_INSERTED)
+    same_state(export_state(t), o.export())
+    assert host(t.contains(dev(burst))).all() and t.size() == nb * 128
