@@ -368,10 +368,12 @@ def run_ours(args):
     (hkv_copy_state). The K timed steps run in segments of SEG_STEPS steps;
     before each segment every table is restored from its snapshot, outside
     the timed brackets, so each segment starts at the load factor it names
-    (the paper's median-of-runs methodology, Sec. 5.1). A profiled pass then
-    repeats the same segments on the same restored states and batches with
-    per-operation and per-kernel events; the uniform-key control runs
-    CONTROL_RUNS times per table from the snapshot."""
+    (the paper's median-of-runs methodology, Sec. 5.1). Two more passes
+    repeat the same segments on the same restored states and batches: one
+    with an event around every call (the per-lambda rates), one with the
+    library's per-kernel events (kernel times and counters), kept apart
+    because the kernel events lengthen every call; the uniform-key control
+    runs CONTROL_RUNS times per table from the snapshot."""
     import torch
     import paper_2603_17168_gb300 as hkv
     from paper_2603_17168_gb300 import workloads as w
@@ -482,8 +484,20 @@ def run_ours(args):
     units_local = float(steps * len(tables) * 2 * batch)
     ms, units = reduce_max_sum(ms_local, units_local, world, dev)
 
-    # profiled pass: the same segments on the same restored states and
-    # batches, with per-operation events and the library's kernel events
+    # per-operation pass: the same segments on the same restored states and
+    # batches, with an event around every call (the per-lambda rates; the
+    # library's kernel events stay off, since they lengthen every call)
+    nvtx.range_push("per_op")
+    for seg in segments:
+        restore()
+        for i in seg:
+            step(i, per_op=True)
+    torch.cuda.synchronize()
+    nvtx.range_pop()
+    op_ms = {i: [(ev[i][li][0].elapsed_time(ev[i][li][1]), ev[i][li][1].elapsed_time(ev[i][li][2]))
+                 for li in range(len(tables))] for seg in segments for i in seg}
+    # profiled pass: the same again with the library's kernel events (the
+    # per-kernel device times) and its counters
     for t in tables:
         t.sync()
         t.reset_counters()
@@ -493,7 +507,7 @@ def run_ours(args):
     for seg in segments:
         restore()
         for i in seg:
-            step(i, per_op=True)
+            step(i)
     torch.cuda.synchronize()
     nvtx.range_pop()
     for t in tables:
@@ -503,12 +517,10 @@ def run_ours(args):
 
     per_lambda = []
     for li, (lam, t) in enumerate(zip(lambdas, tables)):
-        f_seg = [len(seg) * batch / sum(ev[i][li][0].elapsed_time(ev[i][li][1]) for i in seg)
-                 / 1e6 for seg in segments]
-        u_seg = [len(seg) * batch / sum(ev[i][li][1].elapsed_time(ev[i][li][2]) for i in seg)
-                 / 1e6 for seg in segments]
-        f_ms = sum(ev[i][li][0].elapsed_time(ev[i][li][1]) for seg in segments for i in seg)
-        u_ms = sum(ev[i][li][1].elapsed_time(ev[i][li][2]) for seg in segments for i in seg)
+        f_seg = [len(seg) * batch / sum(op_ms[i][li][0] for i in seg) / 1e6 for seg in segments]
+        u_seg = [len(seg) * batch / sum(op_ms[i][li][1] for i in seg) / 1e6 for seg in segments]
+        f_ms = sum(op_ms[i][li][0] for seg in segments for i in seg)
+        u_ms = sum(op_ms[i][li][1] for seg in segments for i in seg)
         c = t.read_counters()
         fb = op_bytes("find", c, steps, batch, DIM)
         ub = op_bytes("upsert", c, steps, batch, DIM)

@@ -16,15 +16,16 @@
 //   insert    phase I: a warp takes 32 consecutive u and runs a
 //             warp-cooperative victim search for each full-bucket miss: the
 //             minimum (score, key) over the 128 (256) slots, admission
-//             control, a CAS lock on the victim, replacement (Algorithm 2
-//             lines 6-14, Algorithm 3). The next search's score and key
-//             lines are bulk-prefetched into L2;
+//             control, a CAS lock on the victim, replacement (the
+//             full-bucket branch of Algorithm 2, and Algorithm 3). The next
+//             search's score and key lines are bulk-prefetched into L2;
 //   reconcile a victim that was itself inserted by this batch is not an
 //             eviction: its key becomes REJECTED and it is dropped from the
 //             evicted output, which is compacted here;
 //   status    broadcast each distinct key's status to all its occurrences.
-// Phase U finishing before phase I starts is what makes the paper's claim
-// "no update races an eviction" hold for real batches.
+// Phase U finishing before phase I starts is what guarantees, for real
+// batches, that no in-place update of a resident runs while its slot is
+// being evicted (the update/insert group separation of Sec. 3.5).
 //
 // Single-bucket claims are linearisable: while a bucket is full a slot's
 // (score, key) only grows; a victim search that meets a locked slot among
@@ -390,8 +391,8 @@ __device__ __forceinline__ void claim_backoff(int attempt, uint64_t h) {
   __nanosleep(base + ((unsigned)(h >> 17) & 255u));
 }
 
-// Free-slot claim for one missing key, run by one thread (Algorithm 2
-// lines 6-9; Algorithm 3 phase D1: a free slot of the less occupied
+// Free-slot claim for one missing key, run by one thread (the free-slot
+// branch of Algorithm 2; Algorithm 3 phase D1: a free slot of the less occupied
 // candidate bucket, b1 on equal occupancy). Occupancy comes from the
 // per-bucket counters, which count a slot from the moment its claim CAS
 // succeeds, so a counter never exceeds the slots really taken: a counter at
@@ -677,11 +678,10 @@ __device__ __forceinline__ void warp_min_sk(unsigned long long s, unsigned long 
   mine = tied;
 }
 
-// Slot of a bucket held by `lane` in a victim search's coalesced pair reads:
-// q = 0, 1 are slots 2*lane, 2*lane + 1; q = 2, 3 are 64 + 2*lane, 65 + 2*lane.
-__device__ __forceinline__ int held_slot(int lane, int q) {
-  return (q >> 1) * 64 + 2 * lane + (q & 1);
-}
+// Slot of a bucket held by `lane` in a victim search's pair reads: slot
+// 32q + lane for q = 0..3, so each of the warp's four reads covers 512
+// contiguous bytes (16 whole sectors).
+__device__ __forceinline__ int held_slot(int lane, int q) { return 32 * q + lane; }
 
 // Write (key, value, score, digest) into a slot this warp holds LOCKED, then
 // publish the key. The digest and score go first, so other claimers see the
@@ -837,7 +837,7 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
         // Buckets stay full during a batch (no erase runs beside an
         // inserter), so the victim search needs no free-slot re-check.
         // Each lane reads its slots' (key, score) pairs, coalesced (slots
-        // 2l, 2l+1 and 64+2l, 65+2l of each candidate bucket) and keeps
+        // l, 32+l, 64+l and 96+l of each candidate bucket) and keeps
         // its smallest (score, key); one warp argmin gives the victim. A slot
         // locked by another warp is mid-replacement: if its visible score
         // does not exceed the minimum, its next (score, key) could be the
@@ -849,10 +849,10 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
         for (int half = 0; half < 2; ++half) {
           if (half == 1 && !two) break;
           const uint64_t bb = half ? b2 : b1;
-          // (key, score) pairs of the held slots 2l, 2l+1, 64+2l, 65+2l
+          // (key, score) pairs of the held slots 32q + l
           const ulonglong2* pp = reinterpret_cast<const ulonglong2*>(key_ptr(t, bb * kSlots));
-          const ulonglong2 p0 = __ldcg(pp + 2 * lane), p1 = __ldcg(pp + 2 * lane + 1);
-          const ulonglong2 p2 = __ldcg(pp + 64 + 2 * lane), p3 = __ldcg(pp + 65 + 2 * lane);
+          const ulonglong2 p0 = __ldcg(pp + held_slot(lane, 0)), p1 = __ldcg(pp + held_slot(lane, 1));
+          const ulonglong2 p2 = __ldcg(pp + held_slot(lane, 2)), p3 = __ldcg(pp + held_slot(lane, 3));
           const unsigned long long sq[4] = {p0.y, p1.y, p2.y, p3.y};
           const unsigned long long kq[4] = {p0.x, p1.x, p2.x, p3.x};
 #pragma unroll
@@ -1056,8 +1056,8 @@ __device__ __forceinline__ void ordered_insert(const TableDev& t, const Scratch&
         if (half == 1 && !two) break;
         const uint64_t bb = half ? c2 : c1;
         const ulonglong2* pp = reinterpret_cast<const ulonglong2*>(key_ptr(t, bb * kSlots));
-        const ulonglong2 p0 = __ldcg(pp + 2 * lane), p1 = __ldcg(pp + 2 * lane + 1);
-        const ulonglong2 p2 = __ldcg(pp + 64 + 2 * lane), p3 = __ldcg(pp + 65 + 2 * lane);
+        const ulonglong2 p0 = __ldcg(pp + held_slot(lane, 0)), p1 = __ldcg(pp + held_slot(lane, 1));
+        const ulonglong2 p2 = __ldcg(pp + held_slot(lane, 2)), p3 = __ldcg(pp + held_slot(lane, 3));
         const unsigned long long sq[4] = {p0.y, p1.y, p2.y, p3.y};
         const unsigned long long kq[4] = {p0.x, p1.x, p2.x, p3.x};
 #pragma unroll
