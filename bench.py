@@ -83,6 +83,10 @@ def parse_args(argv=None):
     p.add_argument("--serve-pool", type=int, default=512)
     p.add_argument("--serve-peak-requests", type=int, default=4096)
     p.add_argument("--serve-seconds", type=float, default=3.0)
+    p.add_argument("--serve-warm-seconds", type=float, default=0.5,
+                   help="untimed run of each path at each offered load before its measured "
+                        "run (the batched loop captures a graph per new combination of "
+                        "busy tables, once)")
     p.add_argument("--no-served", action="store_true",
                    help="single-table workload: skip the short serving-loop record")
     p.add_argument("--served-seconds", type=float, default=2.0,
@@ -1362,6 +1366,13 @@ def run_serve(args):
     served = {}
     for frac in (0.25, 0.50, 0.90):
         rate = frac * peak_keys_s / mean_n
+        if args.serve_warm_seconds > 0:
+            # steady state: the round combinations this load produces are
+            # captured before its measured runs
+            warm = make(max(64, int(rate * args.serve_warm_seconds)), rate)
+            warm_reqs = hkv.make_requests(warm)
+            srv.run(warm_reqs, batched=True)
+            srv.run(warm_reqs, batched=False)
         n_req = max(64, int(rate * args.serve_seconds))
         items = make(n_req, rate)
         reqs = hkv.make_requests(items)
@@ -1382,6 +1393,7 @@ def run_serve(args):
                        "ring_keys_per_table": 1 << 20, "max_inflight_rounds": 3,
                        "request_pool": len(pool), "mean_request_keys": round(mean_n),
                        "seconds_per_load": args.serve_seconds,
+                       "warm_seconds_per_load": args.serve_warm_seconds,
                        "link_bytes_per_key": {"h2d": round(h2d_pk, 1), "d2h": round(d2h_pk, 1)},
                        "link_gbs": link,
                        "link_bound_bkvs": round(link_bound, 4),
@@ -1400,6 +1412,7 @@ def served_record(args):
     keep = ("p50_ms", "p99_ms", "bkvs", "requests")
     return {"workload": r["config"]["workload"],
             "seconds_per_load": a.serve_seconds,
+            "warm_seconds_per_load": a.serve_warm_seconds,
             "link_bound_bkvs": r["config"]["link_bound_bkvs"],
             "peak_bkvs": {"batched": r["peak"]["batched"]["bkvs"],
                           "plain": r["peak"]["plain"]["bkvs"]},
