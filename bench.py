@@ -1404,15 +1404,27 @@ def run_serve(args):
 def served_record(args):
     """The serving workload's latency half of the metric in the default run:
     the same server, tables and request pool as --workload serve, with
-    args.served_seconds per offered load (the full record uses 60 s)."""
-    import copy
-    a = copy.copy(args)
-    a.serve_seconds = args.served_seconds
-    r = run_serve(a)
+    args.served_seconds per offered load (the full record uses 60 s). It runs
+    as its own process, as a server would: run in the process that has just
+    run the single-table workload, the loop met stalls of tens of
+    milliseconds that a fresh process does not show."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--workload", "serve",
+           "--serve-seconds", str(args.served_seconds),
+           "--serve-warm-seconds", str(args.serve_warm_seconds),
+           "--serve-budget-gib", str(args.serve_budget_gib),
+           "--serve-pool", str(args.serve_pool),
+           "--serve-peak-requests", str(args.serve_peak_requests),
+           "--multi-shrink", str(args.multi_shrink)]
+    env = dict(os.environ)
+    for k in ("RANK", "LOCAL_RANK", "WORLD_SIZE", "LOCAL_WORLD_SIZE"):
+        env.pop(k, None)
+    out = subprocess.run(cmd, stdout=subprocess.PIPE, env=env, text=True, check=True).stdout
+    r = json.loads([x for x in out.splitlines() if x.startswith("{")][-1])
     keep = ("p50_ms", "p99_ms", "bkvs", "requests")
     return {"workload": r["config"]["workload"],
-            "seconds_per_load": a.serve_seconds,
-            "warm_seconds_per_load": a.serve_warm_seconds,
+            "process": "own (bench.py --workload serve)",
+            "seconds_per_load": args.served_seconds,
+            "warm_seconds_per_load": args.serve_warm_seconds,
             "link_bound_bkvs": r["config"]["link_bound_bkvs"],
             "peak_bkvs": {"batched": r["peak"]["batched"]["bkvs"],
                           "plain": r["peak"]["plain"]["bkvs"]},
