@@ -1405,9 +1405,9 @@ def served_record(args):
     """The serving workload's latency half of the metric in the default run:
     the same server, tables and request pool as --workload serve, with
     args.served_seconds per offered load (the full record uses 60 s). It runs
-    as its own process, as a server would: run in the process that has just
-    run the single-table workload, the loop met stalls of tens of
-    milliseconds that a fresh process does not show."""
+    as its own process, as a server would, so nothing the single-table run
+    left in this process (its contexts' memory, threads, pinned buffers)
+    shares the host with the loop."""
     cmd = [sys.executable, os.path.abspath(__file__), "--workload", "serve",
            "--serve-seconds", str(args.served_seconds),
            "--serve-warm-seconds", str(args.serve_warm_seconds),
