@@ -554,6 +554,9 @@ def run_ours(args):
             e["ms"] += kms
             e["launches"] += launches
             e["bytes"] += kernel_bytes(kind, c, steps, batch, DIM)
+            if kind == "status" and "reconcile" not in prof:
+                # reconcile and status ran as one cooperative launch
+                e["bytes"] += kernel_bytes("reconcile", c, steps, batch, DIM)
             ra = kernel_random_accesses(kind, c, steps, batch, DIM)
             if ra is not None:
                 acc = e["ra"] or dict.fromkeys(ra, 0)

@@ -22,7 +22,9 @@
 //   reconcile a victim that was itself inserted by this batch is not an
 //             eviction: its key becomes REJECTED and it is dropped from the
 //             evicted output, which is compacted here;
-//   status    broadcast each distinct key's status to all its occurrences.
+//   status    broadcast each distinct key's status to all its occurrences
+//             (reconcile and status run as one cooperative launch,
+//             finish_kernel, on the plain path).
 // Phase U finishing before phase I starts is what guarantees, for real
 // batches, that no in-place update of a resident runs while its slot is
 // being evicted (the update/insert group separation of Sec. 3.5).
@@ -1285,12 +1287,13 @@ constexpr int kRecPerThread = 4;  // distinct keys a thread has in flight per ro
 // takes kRecPerThread keys per thread, strided by the grid: their loads and
 // dedup-chain walks are in flight together, and one list reservation per
 // block covers all of them.
-__global__ void __launch_bounds__(kRecThreads)
-    reconcile_kernel(TableDev t, Scratch s, uint64_t* __restrict__ ev_keys,
-                     uint64_t* __restrict__ ev_scores, float* __restrict__ ev_values) {
-  if (aborted(s)) return;
-  // Phase U placed every key, so no key displaced anything (grid-uniform)
-  if (s.cnt[kCntDeferred] == 0) return;
+// The reconcile pass over the batch's distinct keys, by every block of the
+// launch (grid-stride); the caller has checked that the batch is live and
+// that phase I ran.
+__device__ __forceinline__ void reconcile_body(const TableDev& t, const Scratch& s,
+                                               uint64_t* __restrict__ ev_keys,
+                                               uint64_t* __restrict__ ev_scores,
+                                               float* __restrict__ ev_values) {
   const int tab_bits = s.d ? tab_bits_for(s.d->n) : s.tab_bits;
   const uint64_t tab_mask = (1ull << tab_bits) - 1;
   const uint64_t nu = s.cnt[kCntUnique];
@@ -1356,6 +1359,15 @@ __global__ void __launch_bounds__(kRecThreads)
   }
 }
 
+__global__ void __launch_bounds__(kRecThreads)
+    reconcile_kernel(TableDev t, Scratch s, uint64_t* __restrict__ ev_keys,
+                     uint64_t* __restrict__ ev_scores, float* __restrict__ ev_values) {
+  if (aborted(s)) return;
+  // Phase U placed every key, so no key displaced anything (grid-uniform)
+  if (s.cnt[kCntDeferred] == 0) return;
+  reconcile_body(t, s, ev_keys, ev_scores, ev_values);
+}
+
 constexpr int kStatusPerThread = 4;  // positions a thread has in flight per round
 
 // Deferred rows (tables with host-memory slices). A slot in host memory
@@ -1389,9 +1401,11 @@ __global__ void __launch_bounds__(kFlushThreads)
   }
 }
 
-__global__ void status_kernel(uint64_t n, Scratch s, uint8_t* __restrict__ status_out,
-                              uint64_t* __restrict__ n_evicted) {
-  if (aborted(s)) return;
+// The status broadcast, by every block of the launch (grid-stride), on a
+// live batch.
+__device__ __forceinline__ void status_body(uint64_t n, const Scratch& s,
+                                            uint8_t* __restrict__ status_out,
+                                            uint64_t* __restrict__ n_evicted) {
   if (s.d) {
     n = s.d->n;
     status_out = s.d->flags;
@@ -1417,6 +1431,30 @@ __global__ void status_kernel(uint64_t n, Scratch s, uint8_t* __restrict__ statu
     }
   }
   if (n_evicted && blockIdx.x == 0 && threadIdx.x == 0) *n_evicted = s.cnt[kCntEvOut];
+}
+
+__global__ void status_kernel(uint64_t n, Scratch s, uint8_t* __restrict__ status_out,
+                              uint64_t* __restrict__ n_evicted) {
+  if (aborted(s)) return;
+  status_body(n, s, status_out, n_evicted);
+}
+
+// Reconcile and status in one cooperative launch (the plain upsert path):
+// below lambda 1 phase U places every key and the reconcile pass has nothing
+// to do, so the launch is the status broadcast alone; otherwise a grid
+// barrier separates the two passes (status reads what reconcile settled).
+// The batch's abort flag and deferred count were set by earlier kernels, so
+// every block takes the same branch and meets the barrier.
+__global__ void __launch_bounds__(kRecThreads)
+    finish_kernel(TableDev t, Scratch s, uint64_t* __restrict__ ev_keys,
+                  uint64_t* __restrict__ ev_scores, float* __restrict__ ev_values, uint64_t n,
+                  uint8_t* __restrict__ status_out, uint64_t* __restrict__ n_evicted) {
+  if (aborted(s)) return;
+  if (s.cnt[kCntDeferred] != 0) {
+    reconcile_body(t, s, ev_keys, ev_scores, ev_values);
+    if (!grid_barrier(s, t.err)) return;
+  }
+  status_body(n, s, status_out, n_evicted);
 }
 
 // -------------------------------------------------------------------- erase
@@ -1652,6 +1690,37 @@ hkv_status run_ordered_phase_i(hkv_table_s* t, uint64_t n, const Scratch& s, con
 
 }  // namespace
 
+// Reconcile and status of a plain upsert as one cooperative launch
+// (finish_kernel); false if the launch was refused, and the caller launches
+// the two kernels instead.
+bool launch_finish(hkv_table_s* t, uint64_t n, const Scratch& s, uint64_t* ev_keys,
+                   uint64_t* ev_scores, float* ev_values, uint8_t* status_out,
+                   uint64_t* n_evicted, cudaStream_t st) {
+  static const int per_sm = [] {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, finish_kernel, kRecThreads, 0) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      b = 0;
+    }
+    return b;
+  }();
+  if (per_sm <= 0) return false;
+  const unsigned grid = (unsigned)std::max<uint64_t>(
+      1, std::min<uint64_t>((uint64_t)t->num_sms * (unsigned)per_sm,
+                            (n + kRecThreads * kRecPerThread - 1) / (kRecThreads * kRecPerThread)));
+  TableDev dv = t->dev;
+  Scratch sv = s;
+  uint64_t nn = n;
+  void* args[] = {&dv, &sv, &ev_keys, &ev_scores, &ev_values, &nn, &status_out, &n_evicted};
+  KernelTimer timer(t->prof, HKV_K_STATUS, st);
+  if (cudaLaunchCooperativeKernel(reinterpret_cast<void*>(finish_kernel), grid, kRecThreads, args,
+                                  0, st) == cudaSuccess)
+    return true;
+  cudaGetLastError();
+  return false;
+}
+
 hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const float* values,
                          const uint64_t* scores, uint8_t* status_out, uint64_t* ev_keys,
                          uint64_t* ev_scores, float* ev_values, uint64_t* n_evicted,
@@ -1707,14 +1776,16 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
         flush_deferred_rows_kernel<false><<<fg, kFlushThreads, 0, st>>>(t->dev, s, ro, values);
     }
   }
-  {
-    KernelTimer timer(t->prof, HKV_K_RECONCILE, st);
-    reconcile_kernel<<<reconcile_grid(t, n), kRecThreads, 0, st>>>(
-        t->dev, s, ev_keys, ev_scores, ev_values);
-  }
-  if (status_out || n_evicted) {
-    KernelTimer timer(t->prof, HKV_K_STATUS, st);
-    status_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(n, s, status_out, n_evicted);
+  if (!launch_finish(t, n, s, ev_keys, ev_scores, ev_values, status_out, n_evicted, st)) {
+    {
+      KernelTimer timer(t->prof, HKV_K_RECONCILE, st);
+      reconcile_kernel<<<reconcile_grid(t, n), kRecThreads, 0, st>>>(
+          t->dev, s, ev_keys, ev_scores, ev_values);
+    }
+    if (status_out || n_evicted) {
+      KernelTimer timer(t->prof, HKV_K_STATUS, st);
+      status_kernel<<<grid_for(t, n, 256, 8), 256, 0, st>>>(n, s, status_out, n_evicted);
+    }
   }
   cudaFreeAsync(a.base, st);
   return cuda_status(cudaGetLastError(), "insert_or_assign launch");
