@@ -557,6 +557,10 @@ def run_ours(args):
             if kind == "status" and "reconcile" not in prof:
                 # reconcile and status ran as one cooperative launch
                 e["bytes"] += kernel_bytes("reconcile", c, steps, batch, DIM)
+            if kind == "insert" and "status" not in prof and "reconcile" not in prof:
+                # phase I, reconcile and status ran as one cooperative launch
+                e["bytes"] += (kernel_bytes("reconcile", c, steps, batch, DIM)
+                               + kernel_bytes("status", c, steps, batch, DIM))
             ra = kernel_random_accesses(kind, c, steps, batch, DIM)
             if ra is not None:
                 acc = e["ra"] or dict.fromkeys(ra, 0)

@@ -22,9 +22,10 @@
 //   reconcile a victim that was itself inserted by this batch is not an
 //             eviction: its key becomes REJECTED and it is dropped from the
 //             evicted output, which is compacted here;
-//   status    broadcast each distinct key's status to all its occurrences
-//             (reconcile and status run as one cooperative launch,
-//             finish_kernel, on the plain path).
+//   status    broadcast each distinct key's status to all its occurrences.
+// On the plain path insert, reconcile and status are one cooperative launch
+// (insert_finish_kernel; finish_kernel, reconcile and status only, after the
+// host-row pass of tiered tables).
 // Phase U finishing before phase I starts is what guarantees, for real
 // batches, that no in-place update of a resident runs while its slot is
 // being evicted (the update/insert group separation of Sec. 3.5).
@@ -776,13 +777,12 @@ struct PendingKey {
 
 constexpr int kPrefetchAhead = 1;  // victim searches whose lines are prefetched ahead
 
+// Phase I by every block of the launch, on a live batch whose phase U left
+// keys for it (insert_kernel; insert_finish_kernel).
 template <bool VEC16>
-__global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
-    insert_kernel(TableDev t, Scratch s, const float* __restrict__ values,
-                  const uint64_t* __restrict__ scores_in, ScoreCtx ctx) {
-  if (aborted(s)) return;
-  // Phase U placed every key: no victim search (the same for the whole grid)
-  if (s.cnt[kCntDeferred] == 0) return;
+__device__ __forceinline__ void insert_body(const TableDev& t, const Scratch& s,
+                                            const float* __restrict__ values,
+                                            const uint64_t* __restrict__ scores_in, ScoreCtx ctx) {
   int row_prefetch = s.row_prefetch;
   if (s.d) {
     values = s.d->values_in;
@@ -992,6 +992,16 @@ __global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
   const unsigned vals[7] = {inserted, lane == 0 ? evicted : 0u, lane == 0 ? rejected : 0u,
                             retries, 0u, lane == 0 ? score_lines : 0u, 0u};
   flush_counts(t, which, vals);
+}
+
+template <bool VEC16>
+__global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
+    insert_kernel(TableDev t, Scratch s, const float* __restrict__ values,
+                  const uint64_t* __restrict__ scores_in, ScoreCtx ctx) {
+  if (aborted(s)) return;
+  // Phase U placed every key: no victim search (the same for the whole grid)
+  if (s.cnt[kCntDeferred] == 0) return;
+  insert_body<VEC16>(t, s, values, scores_in, ctx);
 }
 
 // ------------------------------------------------- ordered phase I (waves)
@@ -1457,6 +1467,29 @@ __global__ void __launch_bounds__(kRecThreads)
   status_body(n, s, status_out, n_evicted);
 }
 
+// Phase I, reconcile and status in one cooperative launch (plain upserts of
+// tables without host rows or ordered waves): below lambda 1 phase U placed
+// every key and the launch is the status broadcast alone, one launch where
+// there were two; otherwise grid barriers separate the three passes. Phase I
+// latches its timeouts without setting the abort flag, so every block takes
+// the same branch and meets both barriers.
+template <bool VEC16>
+__global__ void __launch_bounds__(kInsThreads, kInsBlocksPerSm)
+    insert_finish_kernel(TableDev t, Scratch s, const float* __restrict__ values,
+                         const uint64_t* __restrict__ scores_in, ScoreCtx ctx,
+                         uint64_t* __restrict__ ev_keys, uint64_t* __restrict__ ev_scores,
+                         float* __restrict__ ev_values, uint64_t n,
+                         uint8_t* __restrict__ status_out, uint64_t* __restrict__ n_evicted) {
+  if (aborted(s)) return;
+  if (s.cnt[kCntDeferred] != 0) {
+    insert_body<VEC16>(t, s, values, scores_in, ctx);
+    if (!grid_barrier(s, t.err)) return;
+    reconcile_body(t, s, ev_keys, ev_scores, ev_values);
+    if (!grid_barrier(s, t.err)) return;
+  }
+  status_body(n, s, status_out, n_evicted);
+}
+
 // -------------------------------------------------------------------- erase
 
 __global__ void validate_kernel(uint64_t n, const uint64_t* __restrict__ keys, Scratch s,
@@ -1690,6 +1723,59 @@ hkv_status run_ordered_phase_i(hkv_table_s* t, uint64_t n, const Scratch& s, con
 
 }  // namespace
 
+// Phase I, reconcile and status of a plain upsert as one cooperative launch
+// (insert_finish_kernel); false if the launch was refused, and the caller
+// launches insert_kernel and the finish instead.
+template <bool VEC16>
+bool launch_insert_finish_t(hkv_table_s* t, uint64_t n, const Scratch& s, const float* values,
+                            const uint64_t* scores, ScoreCtx ctx, uint64_t* ev_keys,
+                            uint64_t* ev_scores, float* ev_values, uint8_t* status_out,
+                            uint64_t* n_evicted, cudaStream_t st) {
+  static const int per_sm = [] {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, insert_finish_kernel<VEC16>, kInsThreads,
+                                                      0) != cudaSuccess) {
+      cudaGetLastError();
+      b = 0;
+    }
+    return b;
+  }();
+  if (per_sm <= 0) return false;
+  const unsigned grid = grid_for(t, (n + 31) / 32 * 32, kInsThreads,
+                                 std::min(per_sm, kInsBlocksPerSm));
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kInsThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2]{};
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  unsigned na = 1;
+  if (t->l2win.num_bytes) {
+    attr[1].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[1].val.accessPolicyWindow = t->l2win;
+    na = 2;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
+  KernelTimer timer(t->prof, HKV_K_INSERT, st);
+  if (cudaLaunchKernelEx(&cfg, insert_finish_kernel<VEC16>, t->dev, s, values, scores, ctx,
+                         ev_keys, ev_scores, ev_values, n, status_out, n_evicted) == cudaSuccess)
+    return true;
+  cudaGetLastError();
+  return false;
+}
+
+bool launch_insert_finish(hkv_table_s* t, uint64_t n, const Scratch& s, const float* values,
+                          const uint64_t* scores, ScoreCtx ctx, bool vec16, uint64_t* ev_keys,
+                          uint64_t* ev_scores, float* ev_values, uint8_t* status_out,
+                          uint64_t* n_evicted, cudaStream_t st) {
+  return vec16 ? launch_insert_finish_t<true>(t, n, s, values, scores, ctx, ev_keys, ev_scores,
+                                              ev_values, status_out, n_evicted, st)
+               : launch_insert_finish_t<false>(t, n, s, values, scores, ctx, ev_keys, ev_scores,
+                                               ev_values, status_out, n_evicted, st);
+}
+
 // Reconcile and status of a plain upsert as one cooperative launch
 // (finish_kernel); false if the launch was refused, and the caller launches
 // the two kernels instead.
@@ -1744,12 +1830,19 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
         s, gather_src, const_cast<float*>(values), t->dev.dim, vec16 ? 1 : 0);
   }
   launch_update<true>(t, n, s, values, scores, ctx, vec16, st);
+  // without host rows or ordered waves, phase I, reconcile and status run
+  // as one cooperative launch
+  bool finished = false;
   if (s.owner) {
     rc = run_ordered_phase_i(t, n, s, values, scores, ctx, vec16, st);
     if (rc) {
       cudaFreeAsync(a.base, st);
       return rc;
     }
+  } else if (!s.gdefer && launch_insert_finish(t, n, s, values, scores, ctx, vec16, ev_keys,
+                                                ev_scores, ev_values, status_out, n_evicted,
+                                                st)) {
+    finished = true;
   } else {
     const unsigned ig = grid_for(t, (n + 31) / 32 * 32, kInsThreads, kInsBlocksPerSm);
     KernelTimer timer(t->prof, HKV_K_INSERT, st);
@@ -1776,7 +1869,8 @@ hkv_status launch_upsert(hkv_table_s* t, uint64_t n, const uint64_t* keys, const
         flush_deferred_rows_kernel<false><<<fg, kFlushThreads, 0, st>>>(t->dev, s, ro, values);
     }
   }
-  if (!launch_finish(t, n, s, ev_keys, ev_scores, ev_values, status_out, n_evicted, st)) {
+  if (!finished &&
+      !launch_finish(t, n, s, ev_keys, ev_scores, ev_values, status_out, n_evicted, st)) {
     {
       KernelTimer timer(t->prof, HKV_K_RECONCILE, st);
       reconcile_kernel<<<reconcile_grid(t, n), kRecThreads, 0, st>>>(
