@@ -168,3 +168,45 @@ def test_inserters_updaters_and_readers_on_their_own_streams():
     assert np.array_equal(gk, rk) and np.array_equal(gs, rs)
     assert np.array_equal(gv.view(np.uint32), rv.view(np.uint32))
     assert t.size() == base.size + sum(f.size for f in fresh)
+
+
+def test_tables_upserting_at_once_on_their_own_streams():
+    """Several tables take full-bucket upserts at the same time, one host
+    thread and stream each, so their cooperative phase-I launches (phase I,
+    reconcile and status with grid barriers between them) run side by side.
+    No call may fail, and each table must end exactly as a twin fed the same
+    batches serially: single-bucket results do not depend on the schedule."""
+    rng = np.random.default_rng(4400)
+    nb, dim, ntab, nbat, n = 64, 8, 4, 6, 20000
+    z = w.Zipf(1.05, 60000)
+    tabs = [hkv.Table(nb * 128, dim, hkv.LFU) for _ in range(ntab)]
+    twins = [hkv.Table(nb * 128, dim, hkv.LFU) for _ in range(ntab)]
+    batches = [[(dev(z.keys(rng, n)), dev(w.normal_values(rng, n, dim)))
+                for _ in range(nbat)] for _ in range(ntab)]
+    torch.cuda.synchronize()
+    errors = []
+
+    def work(i):
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                for k, v in batches[i]:
+                    tabs[i].insert_or_assign(k, v)
+                tabs[i].sync()
+        except Exception as e:  # reported below, on the test's thread
+            errors.append((i, repr(e)))
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(ntab)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
+    for i in range(ntab):
+        for k, v in batches[i]:
+            twins[i].insert_or_assign(k, v)
+        twins[i].sync()
+        assert tabs[i].size() == tabs[i].capacity
+        same_state(export_state(tabs[i]), export_state(twins[i]))
+    for t in tabs + twins:
+        t.close()
