@@ -276,6 +276,21 @@ def kernel_bytes(kind: str, c: dict, n_calls: int, batch: int, dim: int) -> floa
     return 0.0
 
 
+def kind_bytes(kind: str, launched: set, c: dict, n_calls: int, batch: int, dim: int) -> float:
+    """Algorithmic bytes of one kernel kind's launches. On the plain upsert
+    path one cooperative launch runs phase I, reconcile and status (profiled
+    as insert; reconcile and status then have no launches of their own), or,
+    after the host-row pass of tiered tables, reconcile and status (profiled
+    as status): such a kind carries the bytes of every pass it ran."""
+    b = kernel_bytes(kind, c, n_calls, batch, dim)
+    if kind == "status" and "reconcile" not in launched:
+        b += kernel_bytes("reconcile", c, n_calls, batch, dim)
+    if kind == "insert" and "status" not in launched and "reconcile" not in launched:
+        b += (kernel_bytes("reconcile", c, n_calls, batch, dim)
+              + kernel_bytes("status", c, n_calls, batch, dim))
+    return b
+
+
 RANDOM_KINDS = ("line_reads", "sector_reads", "line_writes", "sector_writes")
 
 
@@ -553,14 +568,7 @@ def run_ours(args):
             e = kinds.setdefault(kind, {"ms": 0.0, "launches": 0, "bytes": 0.0, "ra": None})
             e["ms"] += kms
             e["launches"] += launches
-            e["bytes"] += kernel_bytes(kind, c, steps, batch, DIM)
-            if kind == "status" and "reconcile" not in prof:
-                # reconcile and status ran as one cooperative launch
-                e["bytes"] += kernel_bytes("reconcile", c, steps, batch, DIM)
-            if kind == "insert" and "status" not in prof and "reconcile" not in prof:
-                # phase I, reconcile and status ran as one cooperative launch
-                e["bytes"] += (kernel_bytes("reconcile", c, steps, batch, DIM)
-                               + kernel_bytes("status", c, steps, batch, DIM))
+            e["bytes"] += kind_bytes(kind, set(prof), c, steps, batch, DIM)
             ra = kernel_random_accesses(kind, c, steps, batch, DIM)
             if ra is not None:
                 acc = e["ra"] or dict.fromkeys(ra, 0)

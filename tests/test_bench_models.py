@@ -101,3 +101,21 @@ def test_oracle_baseline_splits_find_over_cores_and_times_the_tiny_run():
     assert r["kind"] == "oracle" and r["cores"] >= 1 and r["value"] > 0
     assert r["find_bkvs"] > 0 and r["upsert_bkvs"] > 0
     assert 0 < bench.tiny_whole_run_seconds() < 60
+
+
+def test_fused_launches_carry_the_passes_they_ran():
+    n, dim = 1000, 32
+    c = counters(unique=800, inserted=500, evicted=300, rejected=20, ins_score_lines=600)
+    ins = bench.kernel_bytes("insert", c, 1, n, dim)
+    rec = bench.kernel_bytes("reconcile", c, 1, n, dim)
+    st = bench.kernel_bytes("status", c, 1, n, dim)
+    assert rec > 0 and st > 0
+    # phase I, reconcile and status in one launch, profiled as insert
+    assert bench.kind_bytes("insert", {"insert", "update"}, c, 1, n, dim) == ins + rec + st
+    # reconcile and status in one launch after a separate phase I
+    assert bench.kind_bytes("insert", {"insert", "status"}, c, 1, n, dim) == ins
+    assert bench.kind_bytes("status", {"insert", "status"}, c, 1, n, dim) == st + rec
+    # every pass in its own launch
+    every = {"insert", "reconcile", "status"}
+    assert bench.kind_bytes("status", every, c, 1, n, dim) == st
+    assert bench.kind_bytes("insert", every, c, 1, n, dim) == ins
