@@ -519,9 +519,13 @@ enum {
   HKV_K_FIND = 0,
   HKV_K_DEDUP = 1,
   HKV_K_UPDATE = 2,
-  HKV_K_INSERT = 3,
+  HKV_K_INSERT = 3,     /* insert_or_assign's phase I; on tables without host
+                           slices or ordered waves one cooperative launch that
+                           also runs the reconcile and status passes, which
+                           then record no launches of their own */
   HKV_K_RECONCILE = 4,
-  HKV_K_STATUS = 5,
+  HKV_K_STATUS = 5,     /* after the host-row pass of a tiered table: one
+                           launch that also runs the reconcile pass */
   HKV_K_ERASE = 6,
   HKV_K_EXPORT = 7,
   HKV_K_SIZE = 8,
